@@ -1,0 +1,370 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test names the passage it checks.  None of them compares the oracle with
+itself: they use closed forms (Hankel Green's function), textbook special
+cases (the 5/7-point Laplacian when sigma = 0), exactness statements of the
+paper (Lemma 2.1 / Theorems 3.1, 4.1 with an untruncated local solver; the
+two-layer claims of Section 5.2.2), the narrative of Sections 3-4 (routing,
+sweep supports, transfer counts), and the definition of the gradient (central
+finite differences).
+"""
+import dataclasses
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+from scipy.special import hankel1
+
+import workloads as W
+from oracle import adjoint as ADJ
+from oracle import ddm as D
+from oracle import helmholtz as H
+from oracle import krylov as K
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def _bj(wl):
+    _, J = H.global_operator(wl)
+    return wl.f * J.reshape((1,) + wl.f.shape[1:])
+
+
+# --------------------------------------------------------------------------- operator
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_operator_without_pml_is_textbook_laplacian(ndim):
+    """sigma0 = 0: Eq. 2.2 reduces to Delta u + kappa^2 u, whose second-order
+    central difference (Section 5) is the Kronecker sum of 1-D [1,-2,1]/h^2
+    matrices with Dirichlet ends."""
+    n = (7, 6, 5)[:ndim]
+    wl = W.small_2d() if ndim == 2 else W.small_3d()
+    pml = 2
+    m = np.random.default_rng(0).uniform(0.5, 2.0, size=tuple(reversed([k + 2 * pml for k in n])))
+    wl = dataclasses.replace(wl, n=n, pml=pml, sigma0=0.0, m=m, ndim=ndim)
+    A, J = H.global_operator(wl)
+    N = wl.N
+    ops = [sp.diags([np.ones(k - 1), -2 * np.ones(k), np.ones(k - 1)], [-1, 0, 1]) / wl.h ** 2
+           for k in N]
+    L = sp.csr_matrix((int(np.prod(N)),) * 2)
+    for a in range(ndim):
+        mats = [sp.identity(k) for k in reversed(N)]
+        mats[ndim - 1 - a] = ops[a]
+        T = mats[0]
+        for M_ in mats[1:]:
+            T = sp.kron(T, M_)
+        L = L + T
+    L = L + sp.diags(wl.omega ** 2 * m.ravel())
+    assert np.allclose(J, 1.0)
+    assert abs(A - L).max() < 1e-9 * abs(L).max()
+
+
+def test_operator_complex_symmetric():
+    """The J-multiplied form of Eq. 2.2 is complex symmetric (A^T = A)."""
+    wl = W.small_2d(medium="layered")
+    A, _ = H.global_operator(wl)
+    assert abs(A - A.T).max() == 0.0
+    assert abs(A - A.conj().T).max() > 0.0
+
+
+def test_green_function_order2():
+    """Section 5.1: the discrete PML solution converges at order 2 to the exact
+    solution.  For a radial Gaussian of width s and unit amplitude, outside its
+    support  u = -(i/4) H0^(1)(kappa r) * 2 pi s^2 exp(-kappa^2 s^2 / 2)
+    (fundamental solution of Eq. 1.1 with the Sommerfeld condition, Graf's
+    addition theorem).  Error ratios at h, h/2, h/4 must be ~4."""
+    kappa, s = 2 * np.pi * 4, 1.0 / 32
+    errs = []
+    for nh in (64, 128, 256):
+        h, P = 1.0 / nh, nh // 8
+        n = (nh, nh)
+        f = W.gaussian_sources(n, P, h, [(0.5, 0.5)], s)
+        wl = W.Workload("g", 2, n, h, kappa, P, 50.0, 2, (1, 1),
+                        (np.array([0, nh]), np.array([0, nh])), 1, 1,
+                        W.constant_medium(n, P), f)
+        u = H.solve_global(wl)[0]
+        xs = W.node_coords(n, P, h)
+        X, Y = np.meshgrid(xs[0], xs[1])
+        r = np.hypot(X - 0.5, Y - 0.5)
+        mask = (r > 0.15) & (r < 0.35)
+        ue = -(1j / 4) * hankel1(0, kappa * r[mask]) * 2 * np.pi * s * s * np.exp(-kappa ** 2 * s * s / 2)
+        errs.append(np.linalg.norm(u[mask] - ue) / np.linalg.norm(ue))
+    assert errs[0] < 0.05
+    for a, b in zip(errs, errs[1:]):
+        assert 3.6 < a / b < 4.4, errs
+
+
+def test_dense_and_sparse_direct_agree():
+    wl = W.small_2d(nx=14, ny=12, nbx=2, nby=2, pml=4, overlap=2, sub_pml=3)
+    u1 = H.solve_global(wl, dense=True)
+    u2 = H.solve_global(wl)
+    assert rel(u2, u1) < 1e-12
+    A, J = H.global_operator(wl)
+    b = (wl.f.reshape(wl.f.shape[0], -1) * J[None]).T
+    assert np.linalg.norm(A @ u2.reshape(u2.shape[0], -1).T - b) / np.linalg.norm(b) < 1e-13
+
+
+# --------------------------------------------------------------------------- exactness
+@pytest.mark.parametrize("case", ["2d-layered-3x2", "2d-layered-4x3", "3d-layered-2x2x2"])
+def test_sweeps_exact_with_untruncated_local_solver(case):
+    """Lemma 2.1 + Theorem 3.1 / 4.1: with local solves that carry no PML
+    truncation (each subdomain problem solved on the whole grid), Algorithm
+    3.1 / 4.1 reproduces the global solution to rounding, here for a layered
+    medium; likewise the additive Algorithm 2.1 / 2.2."""
+    if case == "2d-layered-3x2":
+        wl = W.small_2d()
+    elif case == "2d-layered-4x3":
+        wl = W.small_2d(nx=60, ny=52, nbx=4, nby=3)
+    else:
+        wl = W.small_3d(n=(14, 12, 12), nb=(2, 2, 2), pml=4, overlap=2, nrhs=1, medium="layered")
+    ug = H.solve_global(wl)
+    part = D.Partition(wl, ideal=True)
+    b = _bj(wl)
+    assert rel(D.diagonal_sweep(part, b), ug) < 1e-12
+    assert rel(D.additive(part, b), ug) < 1e-12
+
+
+def test_subdomain_pml_gap_decreases_with_width():
+    """Section 5: in constant medium the DDM solution differs from the global
+    PML solution only by the truncation of the subdomain PMLs; the gap must
+    fall monotonically as the subdomain PML widens (config-1 geometry)."""
+    base = W.config(1)
+    gaps = []
+    for Wd in (8, 16, 24, 32):
+        P = max(16, Wd)
+        wl = dataclasses.replace(base, sub_pml=Wd, pml=P, m=W.constant_medium(base.n, P),
+                                 f=W.gaussian_sources(base.n, P, base.h, [(0.3, 0.6)], 2 * base.h))
+        gaps.append(rel(D.ddm_solution(wl), H.solve_global(wl)))
+    assert all(a > b for a, b in zip(gaps, gaps[1:])), gaps
+    assert gaps[1] < 5e-4 and gaps[-1] < 1e-4, gaps
+
+
+def _two_layer_gap(wl, iters):
+    A, J = H.global_operator(wl)
+    ug = H.solve_global(wl)
+    b = _bj(wl)
+    part = D.Partition(wl)
+    u = np.zeros_like(b)
+    out = []
+    for _ in range(iters):
+        r = b - (A @ u.reshape(u.shape[0], -1).T).T.reshape(b.shape)
+        u = u + D.diagonal_sweep(part, r)
+        out.append(rel(u, ug))
+    return out
+
+
+def test_two_layer_2x2_one_iteration():
+    """Section 5.2.2: two-layer medium, interface in the upper half, 2x2
+    partition: one application (four sweeps) gives the solution for a source
+    in any subdomain -- up to the same PML-truncation level as constant medium."""
+    for sb in [(0, 0), (1, 0), (0, 1), (1, 1)]:
+        wl = W.two_layer_2d(n=96, pml=16, overlap=6, sub_pml=16, source_box=sb)
+        wlc = dataclasses.replace(wl, m=np.ones_like(wl.m))
+        g = _two_layer_gap(wl, 1)[0]
+        gc = _two_layer_gap(wlc, 1)[0]
+        assert g < max(3 * gc, 2e-4), (sb, g, gc)
+
+
+def test_two_layer_general_partition_needs_two_iterations():
+    """Section 5.2.2: for a general partition with the source above the
+    interface two iterations are needed; below it one suffices."""
+    wl = W.two_layer_2d(n=96, nb=(3, 3), pml=16, overlap=6, sub_pml=16, source_box=(1, 2),
+                        interface_frac=0.5)
+    g = _two_layer_gap(wl, 2)
+    assert g[0] > 1e-2 and g[1] < 1e-4, g
+    wl = W.two_layer_2d(n=96, nb=(3, 3), pml=16, overlap=6, sub_pml=16, source_box=(1, 0),
+                        interface_frac=0.5)
+    assert _two_layer_gap(wl, 1)[0] < 2e-3
+
+
+# --------------------------------------------------------------------------- routing and supports
+def test_routing_table_2d_matches_golden():
+    """Rules 3.1 and 3.2 with 'smallest usable sweep' (Algorithm 3.1) give the
+    table derived by hand from the narrative of Section 3."""
+    tab = D.route(2)
+    S = D.sweep_dirs(2)
+    assert S == [(1, 1), (-1, 1), (1, -1), (-1, -1)]
+    n = 0
+    for line in open(os.path.join(GOLDEN, "routing_2d.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        l, dx, dy, l2 = (int(t) for t in line.split())
+        got = tab[(l - 1, (dx, dy))]
+        assert (0 if got is None else got + 1) == l2, (l, dx, dy)
+        n += 1
+    assert n == 32
+
+
+def test_routing_3d_sorder_and_first_sweep():
+    """Section 4.1: sweep order (Sorder3D); the first sweep uses exactly the 7
+    directions with non-negative components; nothing is routed to an earlier
+    sweep; every direction is usable by some sweep from sweep 1."""
+    S = D.sweep_dirs(3)
+    assert S == [(1, 1, 1), (-1, 1, 1), (1, -1, 1), (-1, -1, 1),
+                 (1, 1, -1), (-1, 1, -1), (1, -1, -1), (-1, -1, -1)]
+    tab = D.route(3)
+    first = {d for d in D.transfer_dirs(3) if tab[(0, d)] == 0}
+    assert first == {d for d in D.transfer_dirs(3) if min(d) >= 0}
+    assert all(v is None or v >= l for (l, _), v in tab.items())
+    assert all(tab[(0, d)] is not None for d in D.transfer_dirs(3))
+    # Rule 4.1 excludes (1,1,-1) from sweep (1,1,1) although the dot product is 1
+    assert tab[(0, (1, 1, -1))] == 4
+
+
+def _single_source_trace(wl, box, nsweeps=None):
+    """Algorithm 3.1/4.1 with untruncated local solves on a source confined to
+    one box; returns the trace."""
+    part = D.Partition(wl, ideal=True)
+    b = _bj(wl)
+    s = part.subs[box]
+    mask = np.zeros(tuple(reversed(wl.N)))
+    sl = tuple(slice(lo, hi) for lo, hi in reversed(s.box))
+    mask[sl] = 1.0
+    b = b * mask[None]
+    trace = {}
+    D.diagonal_sweep(part, b, trace, nsweeps)
+    return part, trace
+
+
+def test_sweep_supports_and_first_steps_2d():
+    """Section 3, 5x5 example with the source in Omega_{3,3}: sweep 1 is
+    non-zero only on Omega_{3..5;3..5}, sweep 2 on Omega_{1..2;3..5}, sweep 3 on
+    Omega_{3..5;1..2}, sweep 4 on Omega_{1..2;1..2}; the origin is solved at
+    step 5 of sweep 1 and the first non-zero solves of sweeps 2, 3, 4 come at
+    steps 6, 6, 7."""
+    n, P = 50, 6
+    wl = W.small_2d(nx=n, ny=n, nbx=5, nby=5, pml=P, overlap=3, sub_pml=4, nrhs=1, medium="const")
+    part, tr = _single_source_trace(wl, (2, 2))
+    S = D.sweep_dirs(2)
+    quad = {0: (range(2, 5), range(2, 5)), 1: (range(0, 2), range(2, 5)),
+            2: (range(2, 5), range(0, 2)), 3: (range(0, 2), range(0, 2))}
+    first = {0: 5, 1: 6, 2: 6, 3: 7}
+    peak = max(np.abs(v[1]).max() for k, v in tr.items() if len(k) == 2)
+    for l in range(4):
+        steps = []
+        for I in part.subs:
+            u = tr[(l, I)][1]
+            nz = np.abs(u).max() > 1e-12 * peak
+            inside = I[0] in quad[l][0] and I[1] in quad[l][1]
+            assert nz == inside, (l, I)
+            if nz:
+                steps.append(D.front_index(I, part.nb, S[l]) + 1)
+        assert min(steps) == first[l]
+
+
+def _outgoing_counts(wl, origin):
+    part, tr = _single_source_trace(wl, origin, nsweeps=1)
+    peak = max(np.abs(v[1]).max() for k, v in tr.items() if len(k) == 2)
+    mags = {}
+    for I in part.subs:
+        u = tr[(0, I)][1]
+        if np.abs(u).max() <= 1e-12 * peak:
+            continue
+        for d in D.transfer_dirs(wl.ndim):
+            if part.neighbour(I, d) is not None:
+                mags[(I, d)] = np.abs(part.psi(I, d, u)).max()
+    top = max(mags.values())
+    counts = {}
+    for (I, d), v in mags.items():
+        key = tuple(i - o for i, o in zip(I, origin))
+        counts[key] = counts.get(key, 0) + (v > 1e-10 * top)
+    return counts
+
+
+def test_transfer_counts_2d():
+    """Section 3: in the first sweep the origin subdomain sends 8 non-zero
+    transfers, a subdomain reached by a horizontal/vertical transfer sends 5,
+    one reached by a corner transfer sends 3."""
+    wl = W.small_2d(nx=50, ny=50, nbx=5, nby=5, pml=6, overlap=3, sub_pml=4, nrhs=1,
+                    medium="const")
+    c = _outgoing_counts(wl, (2, 2))
+    assert c[(0, 0)] == 8 and c[(1, 0)] == 5 and c[(0, 1)] == 5 and c[(1, 1)] == 3
+
+
+def test_transfer_counts_3d():
+    """Section 4.2: in the first sweep the origin sends 26 transfers, axial
+    subdomains 17, octant ones 7.  For planar subdomains the paper prints 12;
+    its own counting (a subdomain reached across k faces sends 2^k 3^(3-k) - 1:
+    26, 17, 7 and 8, 5, 3 in 2D) gives 11, which is what the exact transfers
+    show -- we read the printed 12 as a misprint."""
+    wl = W.small_3d(n=(20, 20, 20), nb=(4, 4, 4), pml=4, overlap=2, nrhs=1)
+    c = _outgoing_counts(wl, (1, 1, 1))
+    assert c[(0, 0, 0)] == 26
+    assert c[(1, 0, 0)] == 17 and c[(0, 1, 0)] == 17 and c[(0, 0, 1)] == 17
+    assert c[(1, 1, 0)] == 11 and c[(0, 1, 1)] == 11 and c[(1, 0, 1)] == 11
+    assert c[(1, 1, 1)] == 7
+
+
+# --------------------------------------------------------------------------- planted mistakes
+def test_planted_mistakes_break_the_exactness_pin(monkeypatch):
+    """The exactness pin is sensitive: dropping Rule 3.2, or evaluating the
+    cutoff at the node centre beta_hat((m + 1/2)/d) instead of beta_hat(m/d),
+    both make Algorithm 3.1 miss the global solution."""
+    wl = W.small_2d()
+    ug = H.solve_global(wl)
+    b = _bj(wl)
+    with monkeypatch.context() as mp:
+        mp.setattr(D, "opposite_block", lambda *a: False)
+        assert rel(D.diagonal_sweep(D.Partition(wl, ideal=True), b), ug) > 1e-3
+    with monkeypatch.context() as mp:
+        orig = D.beta_hat
+        mp.setattr(D, "beta_hat", lambda t: orig(np.asarray(t) + 0.5 / wl.overlap))
+        assert rel(D.diagonal_sweep(D.Partition(wl, ideal=True), b), ug) > 1e-5
+
+
+# --------------------------------------------------------------------------- GMRES and adjoint
+def test_gmres_ddm_reaches_direct_solution():
+    """Remark 1: the DDM as right preconditioner of GMRES in a layered medium
+    converges to the global discrete solution."""
+    wl = W.small_2d(nx=48, ny=40, nbx=3, nby=2, pml=10, overlap=4, sub_pml=10, nrhs=2)
+    A, J = H.global_operator(wl)
+    b = _bj(wl)
+    M = D.DDMPreconditioner(wl)
+    shp = b.shape
+
+    def apply_A(x):
+        return (A @ x.reshape(shp[0], -1).T).T.reshape(shp)
+
+    x, info = K.gmres(apply_A, b, M, rtol=1e-10, restart=20, maxit=40)
+    assert rel(x, H.solve_global(wl)) < 1e-8
+    assert np.all(info["iters"] <= 12)
+
+
+def test_adjoint_gradient_matches_central_differences():
+    """dL/dm_k = -omega^2 Re(conj(lam_k) J_k u_k) equals the central finite
+    difference of the receiver misfit (definition of the derivative)."""
+    wl = W.small_2d(nx=30, ny=26, nbx=2, nby=2, pml=6, overlap=3, sub_pml=6, nrhs=2)
+    rec = np.array([(wl.pml + k, wl.pml + 2) for k in range(2, 28, 3)])
+    m_true = wl.m * (1 + 0.05 * np.random.default_rng(3).standard_normal(wl.m.shape))
+    d = ADJ.receiver_values(H.solve_global(dataclasses.replace(wl, m=m_true)), rec)
+
+    def loss(m):
+        return ADJ.misfit(H.solve_global(dataclasses.replace(wl, m=m)), rec, d)
+
+    u = H.solve_global(wl)
+    A, _ = H.global_operator(wl)
+    lu = __import__("scipy.sparse.linalg", fromlist=["splu"]).splu(A.tocsc())
+
+    def solve(b):
+        return lu.solve(np.ascontiguousarray(b.reshape(b.shape[0], -1).T)).T.reshape(b.shape)
+
+    lam = ADJ.adjoint_solve(solve, ADJ.adjoint_source(u, rec, d))
+    g = ADJ.gradient(wl, u, lam)
+    rng = np.random.default_rng(5)
+    for _ in range(6):
+        k = (int(rng.integers(wl.pml + 2, wl.pml + 24)), int(rng.integers(wl.pml + 2, wl.pml + 28)))
+        eps = 1e-4 * wl.m[k]
+        mp, mm = wl.m.copy(), wl.m.copy()
+        mp[k] += eps
+        mm[k] -= eps
+        fd = (loss(mp) - loss(mm)) / (2 * eps)
+        assert abs(fd - g[k]) <= 1e-4 * abs(g).max(), (k, fd, g[k])
+    # dot-product test <A^{-1} x, y> = <x, A^{-H} y>
+    x = rng.standard_normal(u.shape) + 1j * rng.standard_normal(u.shape)
+    y = rng.standard_normal(u.shape) + 1j * rng.standard_normal(u.shape)
+    lhs = np.vdot(solve(x), y)
+    rhs = np.vdot(x, ADJ.adjoint_solve(solve, y))
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs)

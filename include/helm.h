@@ -1,0 +1,184 @@
+/*
+ * helm.h -- C ABI of libhelm: the diagonal sweeping source-transfer domain
+ * decomposition method for the Helmholtz equation (Leng & Ju, "A diagonal
+ * sweeping domain decomposition method with source transfer for the Helmholtz
+ * equation"), on one GB300 GPU (sm_103a).
+ *
+ * Problem (Section 1, Eq. 1.1):  Delta u + kappa^2 u = f  in R^n, n = 2, 3,
+ * kappa = omega / c(x), Sommerfeld radiation condition (Eq. 1.2), truncated by
+ * a uniaxial PML (Section 2.1, Eq. 2.1-2.2) with alpha_j = 1 + i sigma_j and
+ * sigma(t) = sigma0 (t/L)^power, discretised by second-order central
+ * differences (5-point in 2D, 7-point in 3D; Section 5) in the J-multiplied
+ * form  div(A grad u) + J kappa^2 u = J f.
+ *
+ * Grid conventions (all arrays):
+ *   - The full grid is the interior, n[a] cells per axis, plus pml.width cells
+ *     on every side: N[a] = n[a] + 2*width.  Nodes are cell centred.
+ *   - Arrays over it are row-major with x fastest: index ((z*Ny)+y)*Nx + x.
+ *   - Complex arrays are interleaved complex128 (re, im), laid out
+ *     [rhs][full grid].  Real arrays are float64.
+ *
+ * Memory: every entry point that takes data pointers also takes `mem`:
+ * HELM_MEM_HOST (pageable or pinned host memory; the library copies in and
+ * out, synchronously) or HELM_MEM_DEVICE (CUDA device pointers valid in the
+ * current device's primary context; work is queued on the context's stream
+ * and completed before return).  The caller owns every pointer it passes; the
+ * library copies what it needs and never keeps a caller pointer.
+ *
+ * Errors: every int-returning call returns HELM_OK (0) or a negative code.
+ * On error the context stays usable unless the code is HELM_ERR_CUDA.
+ * helm_strerror() names a code; helm_last_error() gives the last message of
+ * the calling thread.
+ *
+ * Threads and streams: one context must not be used by two host threads at
+ * once.  All device work of a context runs on its stream (helm_config.stream
+ * or a stream the library creates).
+ */
+#ifndef HELM_H
+#define HELM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum helm_status {
+    HELM_OK = 0,
+    HELM_ERR_ARG = -1,            /* invalid argument or unsupported size */
+    HELM_ERR_OOM = -2,            /* device allocation failed */
+    HELM_ERR_NOT_FACTORED = -3,   /* solve before helm_factor */
+    HELM_ERR_NO_CONVERGENCE = -4, /* GMRES hit maxit; output and stats still written */
+    HELM_ERR_TIMEOUT = -5,        /* a bounded device wait expired */
+    HELM_ERR_CUDA = -6,           /* a CUDA runtime call failed */
+    HELM_ERR_NUMERIC = -7         /* NaN/Inf or zero pivot in a factor */
+};
+
+enum helm_precision {
+    HELM_PREC_F64 = 0,   /* complex128 factors and local solves (plain FP64 DDM) */
+    HELM_PREC_MIXED = 1  /* complex64 factors and local solves, FP64 outer GMRES */
+};
+
+enum helm_pml_form {
+    HELM_PML_LITERAL = 0, /* alpha = 1 + i sigma          (Eq. 2.1 as printed) */
+    HELM_PML_OMEGA = 1    /* alpha = 1 + i sigma / omega  (frequency-scaled)  */
+};
+
+enum helm_mem { HELM_MEM_HOST = 0, HELM_MEM_DEVICE = 1 };
+
+typedef struct helm_ctx helm_ctx;
+
+/* Global PML (Section 2.1, Eq. 2.1): `width` cells on each side of the
+ * interior, sigma(t) = sigma0 (t / (width*h))^power at distance t into it. */
+typedef struct {
+    int32_t width;
+    int32_t power;
+    double sigma0;
+    int32_t form; /* enum helm_pml_form */
+} helm_pml;
+
+/* Checkerboard partition (Section 2.1): nb[a] boxes per axis.  cuts[a], if
+ * not NULL, holds nb[a]+1 increasing box faces in interior cells with
+ * cuts[a][0] = 0 and cuts[a][nb[a]] = n[a]; NULL means uniform boxes.  Edge
+ * boxes extend over the global PML.  Each subdomain problem P_{Omega_ij} has
+ * `overlap` (d) cells of zero sigma beyond an internal box face followed by
+ * `sub_pml` PML cells (shifted profile, Eq. 2.3); sub_pml = 0 means
+ * pml.width.  Every box must be at least overlap + 2 cells wide and every
+ * window must stay inside the full grid. */
+typedef struct {
+    int32_t nb[3];
+    const int64_t *cuts[3];
+    int32_t overlap;
+    int32_t sub_pml;
+} helm_partition;
+
+/* Implementation knobs.  Zero-initialise for defaults. */
+typedef struct {
+    int32_t precision;  /* enum helm_precision (default HELM_PREC_MIXED) */
+    int32_t rhs_panel;  /* right-hand sides per CTA in the subdomain solve; 0 = auto */
+    int32_t restart;    /* GMRES restart length; 0 = 30 */
+    int32_t verbose;    /* 1: per-iteration residuals on stderr */
+    void *stream;       /* cudaStream_t to run on; NULL = the library's own stream */
+} helm_config;
+
+typedef struct {
+    int32_t iters;         /* GMRES iterations (max over right-hand sides) */
+    int32_t applications;  /* DDM applications performed */
+    double resid;          /* final relative residual |Jf - Au|/|Jf| (max over RHS) */
+    double t_factor_ms;    /* last helm_factor wall time */
+    double t_solve_ms;     /* this call's wall time */
+    int32_t levels;        /* dependency levels of one DDM application */
+    int32_t solves;        /* subdomain solves of one DDM application */
+} helm_stats;
+
+/* Create a context: copy m (squared slowness 1/c^2, float64, full grid,
+ * host pointer), build the PML coefficients (Eq. 2.1-2.3), the subdomain
+ * windows (Section 2.1), the routing table of transferred sources by Rules
+ * 3.1/3.2 (2D) or 4.1/4.2 (3D) with the smallest-usable-sweep rule of
+ * Algorithm 3.1/4.1, and the dependency levels of one sweep application.
+ * ndim is 2 or 3; n[2] is ignored in 2D.  cfg may be NULL.  On success *out
+ * owns all device memory of the problem. */
+int helm_setup(helm_ctx **out, int ndim, const int64_t n[3], double h, double omega,
+               const double *m, const helm_pml *pml, const helm_partition *part,
+               const helm_config *cfg);
+
+/* Factor every subdomain PML operator L_{ij} (the local problems of
+ * Algorithm 3.1/4.1) as a block-tridiagonal block LU over lines (2D) or
+ * planes (3D): S_1 = A_11, S_j = A_jj - diag(a_j) S_{j-1}^{-1} diag(c_{j-1}),
+ * storing D_j = S_j^{-1} (dense, partial pivoting).  Idempotent. */
+int helm_factor(helm_ctx *ctx);
+
+/* One application of Algorithm 3.1 (2D) / 4.1 (3D) to sources F: returns
+ * u_DDM = sum_l sum_ij beta_{0,0;ij} u^l_ij (Eq. 3.x/4.x).  In constant medium
+ * this is the global PML solution up to subdomain-PML truncation (Theorems
+ * 3.1/4.1).  F, U: complex128 [nrhs][full grid]. */
+int helm_apply_ddm(helm_ctx *ctx, int nrhs, const void *F, void *U, int mem);
+
+/* Solve the global PML system A u = J f for nrhs sources with FP64 flexible
+ * GMRES, right-preconditioned by one DDM application per iteration
+ * (Remark 1), restarted every cfg.restart iterations, until the relative
+ * residual is <= rtol for every right-hand side or maxit iterations.
+ * Returns HELM_ERR_NO_CONVERGENCE (with U and *st written) if maxit is hit.
+ * st may be NULL. */
+int helm_solve(helm_ctx *ctx, int nrhs, const void *F, void *U, int mem, double rtol,
+               int maxit, helm_stats *st);
+
+/* Adjoint solve A^H lambda = g.  A is complex symmetric, so this runs
+ * helm_solve on conj(g) with the same factors and DDM and conjugates the
+ * result.  G, Lambda: complex128 [nrhs][full grid]. */
+int helm_adjoint(helm_ctx *ctx, int nrhs, const void *G, void *Lambda, int mem, double rtol,
+                 int maxit, helm_stats *st);
+
+/* Gradient of L(m) = 1/2 sum_s |P u_s - d_s|^2 with respect to m:
+ * grad_k = -omega^2 sum_s Re(conj(lambda_{s,k}) J_k u_{s,k}), from forward
+ * fields U and adjoint fields Lambda (complex128 [nsrc][full grid]).  grad:
+ * float64 full grid, overwritten. */
+int helm_gradient(helm_ctx *ctx, int nsrc, const void *U, const void *Lambda, double *grad,
+                  int mem);
+
+/* FP64 residual R = J F - A U on the full grid (complex128 [nrhs][grid]). */
+int helm_residual(helm_ctx *ctx, int nrhs, const void *F, const void *U, void *R, int mem);
+
+/* Solve one subdomain PML problem L_s u = r (the local solve of Algorithm
+ * 3.1/4.1) with its stored factors.  s indexes subdomains with x fastest;
+ * R, U: complex128 [nrhs][window], the window being the subdomain's box plus
+ * overlap plus PML (helm_window_info).  For testing the factor and solve. */
+int helm_subdomain_solve(helm_ctx *ctx, int s, int nrhs, const void *R, void *U, int mem);
+
+/* Window of subdomain s: lo[3], hi[3] full-grid node ranges (hi exclusive). */
+int helm_window_info(helm_ctx *ctx, int s, int64_t lo[3], int64_t hi[3]);
+
+/* Number of subdomains, full-grid size N[3] (N[2] = 1 in 2D). */
+int helm_problem_info(helm_ctx *ctx, int64_t *nsub, int64_t N[3]);
+
+/* Bytes of device memory held by the context. */
+int64_t helm_device_bytes(helm_ctx *ctx);
+
+void helm_destroy(helm_ctx *ctx);
+const char *helm_strerror(int code);
+const char *helm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HELM_H */

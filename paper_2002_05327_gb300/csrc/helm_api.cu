@@ -1,0 +1,1084 @@
+// libhelm host side: problem setup, scheduling of Algorithm 3.1 / 4.1 by
+// dependency levels, the factor driver, the DDM application, FP64 flexible
+// GMRES (Remark 1), the adjoint and the C ABI of include/helm.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <functional>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "helm_internal.h"
+
+using namespace helm;
+using cd = std::complex<double>;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? HELM_ERR_OOM : HELM_ERR_CUDA,       \
+                        std::string(#call) + ": " + cudaGetErrorString(e_));                  \
+    } while (0)
+
+#define TRY(call)                  \
+    do {                           \
+        int r_ = (call);           \
+        if (r_ != HELM_OK) return r_; \
+    } while (0)
+
+// ----------------------------------------------------------------------------- PML profile
+// sigma at cell position p for one side: the PML starts `gap` cells beyond
+// `face` and is `width` cells thick (Eq. 2.1; Eq. 2.3 for gap = d).
+struct SideP {
+    double face, gap, width;
+};
+struct AxisP {
+    int lo, hi;
+    SideP left, right;
+};
+
+double sigma_at(double p, const AxisP& ax, double sigma0, int power) {
+    double s = 0.0;
+    double tl = ax.left.face - p;
+    if (tl > ax.left.gap) s += sigma0 * std::pow((tl - ax.left.gap) / ax.left.width, power);
+    double tr = p - ax.right.face;
+    if (tr > ax.right.gap) s += sigma0 * std::pow((tr - ax.right.gap) / ax.right.width, power);
+    return s;
+}
+
+cd alpha_at(double p, const AxisP& ax, const helm_pml& pml, double omega) {
+    double s = sigma_at(p, ax, pml.sigma0, pml.power);
+    if (pml.form == HELM_PML_OMEGA) s /= omega;
+    return cd(1.0, s);
+}
+
+// beta_hat(t) = 1 - (10 t^3 - 15 t^4 + 6 t^5) on [0,1]: a monotone C^2 cutoff.
+double beta_hat(double t) {
+    if (t <= 0) return 1.0;
+    if (t >= 1) return 0.0;
+    return 1.0 - t * t * t * (10.0 - 15.0 * t + 6.0 * t * t);
+}
+
+template <typename T>
+T* dalloc(size_t count, int* rc) {
+    void* p = nullptr;
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        *rc = fail(HELM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        return nullptr;
+    }
+    *rc = HELM_OK;
+    return static_cast<T*>(p);
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------------------- context
+struct helm_ctx {
+    DevProblem P{};
+    int64_t n[3]{};
+    helm_pml pml{};
+    int W = 0;
+    helm_config cfg{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int prec = HELM_PREC_MIXED;
+    int nsweeps = 0;
+
+    std::vector<SubDesc> subs_h;
+    SubDesc* subs_d = nullptr;
+    int nbp_max = 0;
+    int64_t max_win = 0;
+
+    // global problem
+    cplx<double>* g_alpha = nullptr;  // per axis: nodes then faces
+    Win<double> gwin{};
+    double* m64 = nullptr;
+    float* m32 = nullptr;
+    int64_t Ng = 0;
+
+    // subdomain coefficients (double and float copies)
+    cplx<double>* an64 = nullptr;
+    cplx<double>* af64 = nullptr;
+    cplx<float>* an32 = nullptr;
+    cplx<float>* af32 = nullptr;
+    cplx<double>* Pv64 = nullptr;
+    cplx<double>* inva64 = nullptr;
+    cplx<float>* Pv32 = nullptr;
+    cplx<float>* inva32 = nullptr;
+    double* tab64 = nullptr;
+    float* tab32 = nullptr;
+    int* box_of = nullptr;
+
+    // factors
+    void* fac = nullptr;
+    size_t fac_bytes = 0;
+    bool factored = false;
+    double t_factor_ms = 0;
+    int* err_d = nullptr;
+
+    // schedule
+    std::vector<std::vector<Task>> levels;
+    std::vector<int> level_off;
+    Task* tasks_d = nullptr;
+    Incoming* inc_d = nullptr;
+    std::vector<int64_t> node_buf_h;  // (l*nsub + s) -> element offset, or -1 if inactive
+    int64_t* node_buf_d = nullptr;
+    int64_t buf_per_rhs = 0;
+    int nsolves = 0;
+
+    // work buffers
+    int cap_rhs = 0;
+    void* buf = nullptr;           // window buffers, complex T, [rhs][nodes][window]
+    cplx<double>* bvec = nullptr;  // J-scaled source of one DDM application
+    int cap_vec_rhs = 0;
+    std::vector<cplx<double>*> gm;  // GMRES vectors (each nrhs*Ng)
+    int gm_rhs = 0;
+    cplx<double>* small_d = nullptr;  // dots / coefficients
+    cplx<double>* partial_d = nullptr;
+    double* scal_d = nullptr;
+    size_t small_cap = 0;
+    size_t dev_bytes = 0;
+};
+
+namespace {
+
+size_t elem_size(const helm_ctx* c) { return c->prec == HELM_PREC_F64 ? 16 : 8; }
+
+int ensure_buffers(helm_ctx* c, int nrhs) {
+    if (nrhs <= c->cap_rhs && c->buf) return HELM_OK;
+    if (c->buf) {
+        cudaFree(c->buf);
+        c->dev_bytes -= (size_t)c->cap_rhs * c->buf_per_rhs * elem_size(c);
+        c->buf = nullptr;
+    }
+    size_t bytes = (size_t)nrhs * c->buf_per_rhs * elem_size(c);
+    CK(cudaMalloc(&c->buf, bytes));
+    c->dev_bytes += bytes;
+    c->cap_rhs = nrhs;
+    return HELM_OK;
+}
+
+int ensure_bvec(helm_ctx* c, int nrhs) {
+    if (nrhs <= c->cap_vec_rhs && c->bvec) return HELM_OK;
+    if (c->bvec) {
+        cudaFree(c->bvec);
+        c->dev_bytes -= (size_t)c->cap_vec_rhs * c->Ng * 16;
+        c->bvec = nullptr;
+    }
+    CK(cudaMalloc(&c->bvec, (size_t)nrhs * c->Ng * 16));
+    c->dev_bytes += (size_t)nrhs * c->Ng * 16;
+    c->cap_vec_rhs = nrhs;
+    return HELM_OK;
+}
+
+int ensure_small(helm_ctx* c, size_t count) {
+    if (count <= c->small_cap) return HELM_OK;
+    if (c->small_d) cudaFree(c->small_d);
+    if (c->partial_d) cudaFree(c->partial_d);
+    if (c->scal_d) cudaFree(c->scal_d);
+    CK(cudaMalloc(&c->small_d, count * sizeof(cplx<double>)));
+    CK(cudaMalloc(&c->partial_d, count * 1024 * sizeof(cplx<double>)));
+    CK(cudaMalloc(&c->scal_d, count * sizeof(double)));
+    c->small_cap = count;
+    return HELM_OK;
+}
+
+// ----------------------------------------------------------------------------- routing (Rules 3.1/3.2, 4.1/4.2)
+std::vector<std::array<int, 3>> sweep_dirs(int ndim) {
+    std::vector<std::array<int, 3>> S;
+    for (int l = 0; l < (1 << ndim); ++l) {
+        std::array<int, 3> D{0, 0, 0};
+        for (int a = 0; a < ndim; ++a) D[a] = ((l >> a) & 1) ? -1 : 1;
+        S.push_back(D);
+    }
+    return S;
+}
+
+std::vector<std::array<int, 3>> transfer_dirs(int ndim) {
+    std::vector<std::array<int, 3>> out;
+    for (int dz = (ndim == 3 ? 1 : 0); dz >= (ndim == 3 ? -1 : 0); --dz)
+        for (int dy = 1; dy >= -1; --dy)
+            for (int dx = 1; dx >= -1; --dx)
+                if (dx || dy || dz) out.push_back({dx, dy, dz});
+    return out;
+}
+
+// Rule 3.1 (2D): d.D > 0.  Rule 4.1 (3D): d.D > 0 and d(k) D(k) >= 0 for all k.
+bool similar(const std::array<int, 3>& d, const std::array<int, 3>& D, int ndim) {
+    int dot = 0;
+    bool nonneg = true;
+    for (int a = 0; a < ndim; ++a) {
+        dot += d[a] * D[a];
+        nonneg &= d[a] * D[a] >= 0;
+    }
+    return ndim == 2 ? dot > 0 : (dot > 0 && nonneg);
+}
+
+// Rule 3.2 / 4.2: not used in a later sweep if in some coordinate plane the
+// projection of the source direction has exactly one zero and the projected
+// generating and using sweep directions are opposite.
+bool blocked(const std::array<int, 3>& d, const std::array<int, 3>& Dg,
+             const std::array<int, 3>& Du, int ndim) {
+    const int planes2[1][2] = {{0, 1}};
+    const int planes3[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+    int np = ndim == 2 ? 1 : 3;
+    for (int i = 0; i < np; ++i) {
+        int a = ndim == 2 ? planes2[i][0] : planes3[i][0];
+        int b = ndim == 2 ? planes2[i][1] : planes3[i][1];
+        int zeros = (d[a] == 0) + (d[b] == 0);
+        if (zeros == 1 && Dg[a] == -Du[a] && Dg[b] == -Du[b]) return true;
+    }
+    return false;
+}
+
+int route_of(int l, const std::array<int, 3>& d, const std::vector<std::array<int, 3>>& S, int ndim) {
+    for (int l2 = l; l2 < (int)S.size(); ++l2)
+        if (similar(d, S[l2], ndim) && !blocked(d, S[l], S[l2], ndim)) return l2;
+    return -1;
+}
+
+void fill_window_alpha(const AxisP& ax, const helm_pml& pml, double omega, std::vector<cd>& nodes,
+                       std::vector<cd>& faces) {
+    for (int k = ax.lo; k < ax.hi; ++k) nodes.push_back(alpha_at(k + 0.5, ax, pml, omega));
+    for (int k = ax.lo; k <= ax.hi; ++k) faces.push_back(alpha_at((double)k, ax, pml, omega));
+}
+
+template <typename T>
+int upload(T** dst, const void* src, size_t bytes, helm_ctx* c) {
+    CK(cudaMalloc((void**)dst, bytes ? bytes : 1));
+    if (bytes) CK(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
+    c->dev_bytes += bytes;
+    return HELM_OK;
+}
+
+std::vector<cplx<double>> to_c128(const std::vector<cd>& v) {
+    std::vector<cplx<double>> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = {v[i].real(), v[i].imag()};
+    return o;
+}
+std::vector<cplx<float>> to_c64(const std::vector<cd>& v) {
+    std::vector<cplx<float>> o(v.size());
+    for (size_t i = 0; i < v.size(); ++i) o[i] = {(float)v[i].real(), (float)v[i].imag()};
+    return o;
+}
+
+int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega, const double* m,
+               const helm_pml* pml, const helm_partition* part, const helm_config* cfg) {
+    if (ndim != 2 && ndim != 3) return fail(HELM_ERR_ARG, "ndim must be 2 or 3");
+    if (!n || !m || !pml || !part) return fail(HELM_ERR_ARG, "null argument");
+    if (!(h > 0) || !(omega > 0)) return fail(HELM_ERR_ARG, "h and omega must be positive");
+    if (pml->width < 1 || pml->power < 0 || !(pml->sigma0 >= 0))
+        return fail(HELM_ERR_ARG, "invalid PML");
+    if (part->overlap < 1) return fail(HELM_ERR_ARG, "overlap must be >= 1");
+    if (cfg) c->cfg = *cfg;
+    c->prec = (cfg && cfg->precision == HELM_PREC_F64) ? HELM_PREC_F64 : HELM_PREC_MIXED;
+    if (c->cfg.restart <= 0) c->cfg.restart = 30;
+    c->pml = *pml;
+    c->W = part->sub_pml > 0 ? part->sub_pml : pml->width;
+    DevProblem& P = c->P;
+    P.ndim = ndim;
+    P.h = h;
+    P.omega = omega;
+    P.d = part->overlap;
+    const int Wg = pml->width;
+    for (int a = 0; a < 3; ++a) {
+        c->n[a] = a < ndim ? n[a] : 1;
+        if (a < ndim && (n[a] < 1 || n[a] > (1 << 20))) return fail(HELM_ERR_ARG, "bad grid size");
+        P.N[a] = a < ndim ? (int)(n[a] + 2 * Wg) : 1;
+        P.nb[a] = a < ndim ? part->nb[a] : 1;
+        if (a < ndim && (P.nb[a] < 1 || P.nb[a] > 4096)) return fail(HELM_ERR_ARG, "bad nb");
+    }
+    c->Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
+    P.nsub = P.nb[0] * P.nb[1] * P.nb[2];
+    c->nsweeps = 1 << ndim;
+
+    if (c->cfg.stream) {
+        c->stream = (cudaStream_t)c->cfg.stream;
+    } else {
+        CK(cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking));
+        c->own_stream = true;
+    }
+
+    // ---- global alphas
+    std::vector<AxisP> gax(3);
+    std::vector<cd> gall;
+    int64_t goff[3][2];
+    for (int a = 0; a < 3; ++a) {
+        AxisP ax{0, P.N[a], {(double)Wg, 0.0, (double)Wg}, {(double)(Wg + c->n[a]), 0.0, (double)Wg}};
+        gax[a] = ax;
+        std::vector<cd> nodes, faces;
+        if (a < ndim) fill_window_alpha(ax, *pml, omega, nodes, faces);
+        else {
+            nodes.assign(1, cd(1, 0));
+            faces.assign(2, cd(1, 0));
+        }
+        goff[a][0] = gall.size();
+        gall.insert(gall.end(), nodes.begin(), nodes.end());
+        goff[a][1] = gall.size();
+        gall.insert(gall.end(), faces.begin(), faces.end());
+    }
+    auto g128 = to_c128(gall);
+    TRY(upload(&c->g_alpha, g128.data(), g128.size() * sizeof(cplx<double>), c));
+    for (int a = 0; a < 3; ++a) {
+        c->gwin.lo[a] = 0;
+        c->gwin.n[a] = P.N[a];
+        c->gwin.alpha_node[a] = c->g_alpha + goff[a][0];
+        c->gwin.alpha_face[a] = c->g_alpha + goff[a][1];
+    }
+    // ---- medium
+    TRY(upload(&c->m64, m, c->Ng * sizeof(double), c));
+    {
+        std::vector<float> m32(c->Ng);
+        for (int64_t i = 0; i < c->Ng; ++i) m32[i] = (float)m[i];
+        TRY(upload(&c->m32, m32.data(), c->Ng * sizeof(float), c));
+    }
+    // ---- boxes per axis (global node ranges); edge boxes run over the global PML
+    std::vector<std::vector<int>> blo(3), bhi(3);
+    for (int a = 0; a < 3; ++a) {
+        if (a >= ndim) {
+            blo[a] = {0};
+            bhi[a] = {1};
+            continue;
+        }
+        std::vector<int64_t> cut(P.nb[a] + 1);
+        if (part->cuts[a]) {
+            for (int i = 0; i <= P.nb[a]; ++i) cut[i] = part->cuts[a][i];
+            if (cut[0] != 0 || cut[P.nb[a]] != c->n[a]) return fail(HELM_ERR_ARG, "cuts must span 0..n");
+        } else {
+            for (int i = 0; i <= P.nb[a]; ++i) cut[i] = (i * c->n[a]) / P.nb[a];
+        }
+        for (int i = 0; i < P.nb[a]; ++i) {
+            if (cut[i + 1] <= cut[i]) return fail(HELM_ERR_ARG, "cuts must increase");
+            blo[a].push_back(i == 0 ? 0 : (int)(Wg + cut[i]));
+            bhi[a].push_back(i == P.nb[a] - 1 ? P.N[a] : (int)(Wg + cut[i + 1]));
+            if (bhi[a].back() - blo[a].back() < P.d + 2)
+                return fail(HELM_ERR_ARG, "box narrower than overlap + 2");
+        }
+    }
+    std::vector<int> box_of;
+    for (int a = 0; a < ndim; ++a)
+        for (int k = 0; k < P.N[a]; ++k) {
+            int i = 0;
+            while (k >= bhi[a][i]) ++i;
+            box_of.push_back(i);
+        }
+    TRY(upload(&c->box_of, box_of.data(), box_of.size() * sizeof(int), c));
+
+    // ---- subdomain windows and their coefficients
+    std::vector<cd> an, af, pv, ia;
+    c->subs_h.resize(P.nsub);
+    const int slow = ndim - 1;
+    int64_t fac_elems = 0;
+    for (int s = 0; s < P.nsub; ++s) {
+        int I[3] = {s % P.nb[0], (s / P.nb[0]) % P.nb[1], s / (P.nb[0] * P.nb[1])};
+        SubDesc& S = c->subs_h[s];
+        std::memset(&S, 0, sizeof(S));
+        AxisP axs[3];
+        for (int a = 0; a < 3; ++a) {
+            S.ib[a] = I[a];
+            S.box_lo[a] = blo[a][I[a]];
+            S.box_hi[a] = bhi[a][I[a]];
+            if (a >= ndim) {
+                S.lo[a] = 0;
+                S.hi[a] = 1;
+                axs[a] = gax[a];
+            } else {
+                AxisP ax;
+                if (I[a] == 0) {
+                    ax.lo = 0;
+                    ax.left = gax[a].left;
+                } else {
+                    ax.lo = S.box_lo[a] - P.d - c->W;
+                    ax.left = {(double)S.box_lo[a], (double)P.d, (double)c->W};
+                }
+                if (I[a] == P.nb[a] - 1) {
+                    ax.hi = P.N[a];
+                    ax.right = gax[a].right;
+                } else {
+                    ax.hi = S.box_hi[a] + P.d + c->W;
+                    ax.right = {(double)S.box_hi[a], (double)P.d, (double)c->W};
+                }
+                if (ax.lo < 0 || ax.hi > P.N[a])
+                    return fail(HELM_ERR_ARG, "subdomain window leaves the grid (boxes too narrow for overlap + sub_pml)");
+                S.lo[a] = ax.lo;
+                S.hi[a] = ax.hi;
+                axs[a] = ax;
+            }
+            S.nw[a] = S.hi[a] - S.lo[a];
+            S.alpha_off[a] = an.size();
+            S.face_off[a] = af.size();
+            if (a < ndim) {
+                fill_window_alpha(axs[a], *pml, omega, an, af);
+            } else {
+                an.push_back(cd(1, 0));
+                af.push_back(cd(1, 0));
+                af.push_back(cd(1, 0));
+            }
+        }
+        S.nblk = 1;
+        for (int a = 0; a < slow; ++a) S.nblk *= S.nw[a];
+        S.nlines = S.nw[slow];
+        S.nbp = (S.nblk + 31) / 32 * 32;
+        if (S.nbp > 1024) return fail(HELM_ERR_ARG, "subdomain block larger than 1024 nodes");
+        S.win_elems = (int64_t)S.nw[0] * S.nw[1] * S.nw[2];
+        S.fac_off = fac_elems;
+        fac_elems += (int64_t)S.nlines * 2 * S.nbp * S.nbp;
+        // couplings between blocks: Pv[p] = prod_{a<slow} alpha_a(node) / h^2,
+        // inva[j] = 1 / alpha_slow(face j)
+        S.coup_off = pv.size();
+        for (int p = 0; p < S.nblk; ++p) {
+            cd prod(1.0 / (h * h), 0);
+            int rem = p;
+            for (int a = 0; a < slow; ++a) {
+                int xa = rem % S.nw[a];
+                rem /= S.nw[a];
+                prod *= an[S.alpha_off[a] + xa];
+            }
+            pv.push_back(prod);
+        }
+        S.inva_off = ia.size();
+        for (int j = 0; j <= S.nlines; ++j) ia.push_back(1.0 / af[S.face_off[slow] + j]);
+        c->nbp_max = std::max(c->nbp_max, S.nbp);
+        c->max_win = std::max(c->max_win, S.win_elems);
+    }
+    {
+        auto a128 = to_c128(an), f128 = to_c128(af), p128 = to_c128(pv), i128 = to_c128(ia);
+        auto a64 = to_c64(an), f64 = to_c64(af), p64 = to_c64(pv), i64 = to_c64(ia);
+        TRY(upload(&c->an64, a128.data(), a128.size() * 16, c));
+        TRY(upload(&c->af64, f128.data(), f128.size() * 16, c));
+        TRY(upload(&c->Pv64, p128.data(), p128.size() * 16, c));
+        TRY(upload(&c->inva64, i128.data(), i128.size() * 16, c));
+        TRY(upload(&c->an32, a64.data(), a64.size() * 8, c));
+        TRY(upload(&c->af32, f64.data(), f64.size() * 8, c));
+        TRY(upload(&c->Pv32, p64.data(), p64.size() * 8, c));
+        TRY(upload(&c->inva32, i64.data(), i64.size() * 8, c));
+    }
+    {
+        std::vector<double> t64(P.d + 1);
+        std::vector<float> t32(P.d + 1);
+        for (int mm = 0; mm <= P.d; ++mm) {
+            t64[mm] = beta_hat((double)mm / P.d);
+            t32[mm] = (float)t64[mm];
+        }
+        TRY(upload(&c->tab64, t64.data(), t64.size() * 8, c));
+        TRY(upload(&c->tab32, t32.data(), t32.size() * 4, c));
+    }
+    TRY(upload(&c->subs_d, c->subs_h.data(), c->subs_h.size() * sizeof(SubDesc), c));
+    c->fac_bytes = (size_t)fac_elems * (c->prec == HELM_PREC_F64 ? 8 : 4);
+
+    // ---- routing and dependency levels of one application of Algorithm 3.1/4.1
+    auto S = sweep_dirs(ndim);
+    auto dirs = transfer_dirs(ndim);
+    const int L = c->nsweeps, ns = P.nsub;
+    struct Edge {
+        int dir[3], sender, l_src;
+    };
+    std::vector<std::vector<Edge>> inc((size_t)L * ns);
+    for (int l = 0; l < L; ++l)
+        for (int s = 0; s < ns; ++s) {
+            const SubDesc& SD = c->subs_h[s];
+            for (auto& d : dirs) {
+                int J[3];
+                bool ok = true;
+                for (int a = 0; a < 3; ++a) {
+                    J[a] = SD.ib[a] + d[a];
+                    ok &= J[a] >= 0 && J[a] < P.nb[a];
+                }
+                if (!ok) continue;
+                int l2 = route_of(l, d, S, ndim);
+                if (l2 < 0) continue;
+                int r = J[0] + P.nb[0] * (J[1] + P.nb[1] * J[2]);
+                inc[(size_t)l2 * ns + r].push_back({{d[0], d[1], d[2]}, s, l});
+            }
+        }
+    std::vector<char> active((size_t)L * ns, 0);
+    for (int s = 0; s < ns; ++s) active[s] = 1;
+    for (bool changed = true; changed;) {
+        changed = false;
+        for (size_t k = 0; k < active.size(); ++k) {
+            if (active[k]) continue;
+            for (auto& e : inc[k])
+                if (active[(size_t)e.l_src * ns + e.sender]) {
+                    active[k] = 1;
+                    changed = true;
+                    break;
+                }
+        }
+    }
+    std::vector<int> level((size_t)L * ns, -1);
+    std::function<int(size_t)> lev = [&](size_t k) -> int {
+        if (level[k] >= 0) return level[k];
+        int v = 0;
+        for (auto& e : inc[k]) {
+            size_t ks = (size_t)e.l_src * ns + e.sender;
+            if (active[ks]) v = std::max(v, lev(ks) + 1);
+        }
+        level[k] = v;
+        return v;
+    };
+    int nlev = 0;
+    for (size_t k = 0; k < active.size(); ++k)
+        if (active[k]) nlev = std::max(nlev, lev(k) + 1);
+    c->node_buf_h.assign((size_t)L * ns, -1);
+    int64_t off = 0;
+    c->nsolves = 0;
+    for (int l = 0; l < L; ++l)
+        for (int s = 0; s < ns; ++s) {
+            size_t k = (size_t)l * ns + s;
+            if (!active[k]) continue;
+            c->node_buf_h[k] = off;
+            off += c->subs_h[s].win_elems;
+            ++c->nsolves;
+        }
+    c->buf_per_rhs = off;
+    std::vector<Incoming> inc_all;
+    c->levels.assign(nlev, {});
+    for (int l = 0; l < L; ++l)
+        for (int s = 0; s < ns; ++s) {
+            size_t k = (size_t)l * ns + s;
+            if (!active[k]) continue;
+            Task t;
+            t.sweep = l;
+            t.sub = s;
+            t.in_off = (int)inc_all.size();
+            t.buf_off = c->node_buf_h[k];
+            for (auto& e : inc[k]) {
+                size_t ks = (size_t)e.l_src * ns + e.sender;
+                if (!active[ks]) continue;
+                Incoming I;
+                for (int a = 0; a < 3; ++a) I.dir[a] = e.dir[a];
+                I.sender = e.sender;
+                I.sender_buf_off = c->node_buf_h[ks];
+                inc_all.push_back(I);
+            }
+            t.in_cnt = (int)inc_all.size() - t.in_off;
+            c->levels[level[k]].push_back(t);
+        }
+    std::vector<Task> all_tasks;
+    c->level_off.clear();
+    for (auto& lv : c->levels) {
+        c->level_off.push_back((int)all_tasks.size());
+        all_tasks.insert(all_tasks.end(), lv.begin(), lv.end());
+    }
+    c->level_off.push_back((int)all_tasks.size());
+    TRY(upload(&c->tasks_d, all_tasks.data(), all_tasks.size() * sizeof(Task), c));
+    TRY(upload(&c->inc_d, inc_all.data(), inc_all.size() * sizeof(Incoming), c));
+    TRY(upload(&c->node_buf_d, c->node_buf_h.data(), c->node_buf_h.size() * 8, c));
+    CK(cudaMalloc(&c->err_d, sizeof(int)));
+    return HELM_OK;
+}
+
+int auto_panel(const helm_ctx* c, int nrhs) {
+    int p = c->cfg.rhs_panel;
+    if (p <= 0) {
+        p = nrhs >= 64 ? 8 : nrhs >= 16 ? 4 : nrhs >= 4 ? 2 : 1;
+        if (nrhs >= 2 && nrhs < 4) p = 2;
+    }
+    // register budget of solve_kernel: 8 complex64 or 4 complex128 columns per thread
+    const int pmax = c->prec == HELM_PREC_F64 ? 4 : 8;
+    if (p > pmax) p = pmax;
+    int q = 1;
+    while (q < p) q <<= 1;
+    return q;
+}
+
+// One application of Algorithm 3.1 / 4.1 to the J-scaled source b (device,
+// complex128 [nrhs][grid]); the assembled u_DDM goes to U (device).
+int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U) {
+    if (!c->factored) return fail(HELM_ERR_NOT_FACTORED, "call helm_factor first");
+    TRY(ensure_buffers(c, nrhs));
+    const int64_t rs = c->buf_per_rhs;
+    const int panel = auto_panel(c, nrhs);
+    for (size_t lv = 0; lv < c->levels.size(); ++lv) {
+        const Task* t = c->tasks_d + c->level_off[lv];
+        int nt = (int)c->levels[lv].size();
+        if (c->prec == HELM_PREC_F64) {
+            auto* buf = static_cast<cplx<double>*>(c->buf);
+            launch_gather<double>(t, nt, c->max_win, c->subs_d, c->inc_d, c->P, c->m64, c->an64,
+                                  c->af64, c->tab64, b, nrhs, buf, rs, c->stream);
+            launch_solve<double>(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
+                                 static_cast<const double*>(c->fac), c->Pv64, c->inva64, buf, rs,
+                                 c->stream);
+        } else {
+            auto* buf = static_cast<cplx<float>*>(c->buf);
+            launch_gather<float>(t, nt, c->max_win, c->subs_d, c->inc_d, c->P, c->m32, c->an32,
+                                 c->af32, c->tab32, b, nrhs, buf, rs, c->stream);
+            launch_solve<float>(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
+                                static_cast<const float*>(c->fac), c->Pv32, c->inva32, buf, rs,
+                                c->stream);
+        }
+    }
+    if (c->prec == HELM_PREC_F64)
+        launch_assemble<double>(c->P, c->subs_d, c->box_of, c->node_buf_d, c->nsweeps, c->tab64,
+                                static_cast<const cplx<double>*>(c->buf), rs, nrhs, U, c->stream);
+    else
+        launch_assemble<float>(c->P, c->subs_d, c->box_of, c->node_buf_d, c->nsweeps, c->tab32,
+                               static_cast<const cplx<float>*>(c->buf), rs, nrhs, U, c->stream);
+    CK(cudaGetLastError());
+    return HELM_OK;
+}
+
+// ---- host <-> device staging of caller data
+struct Staged {
+    cplx<double>* ptr = nullptr;
+    bool owned = false;
+    ~Staged() {
+        if (owned && ptr) cudaFree(ptr);
+    }
+};
+
+int stage_in(helm_ctx* c, const void* src, size_t bytes, int mem, Staged& out) {
+    if (mem == HELM_MEM_DEVICE) {
+        out.ptr = (cplx<double>*)src;
+        out.owned = false;
+        return HELM_OK;
+    }
+    if (mem != HELM_MEM_HOST) return fail(HELM_ERR_ARG, "mem must be HELM_MEM_HOST or HELM_MEM_DEVICE");
+    CK(cudaMalloc(&out.ptr, bytes));
+    out.owned = true;
+    if (src) CK(cudaMemcpyAsync(out.ptr, src, bytes, cudaMemcpyHostToDevice, c->stream));
+    return HELM_OK;
+}
+
+int stage_out(helm_ctx* c, void* dst, const Staged& s, size_t bytes, int mem) {
+    if (mem == HELM_MEM_HOST) CK(cudaMemcpyAsync(dst, s.ptr, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    return HELM_OK;
+}
+
+int ensure_gm(helm_ctx* c, int nrhs, int count) {
+    if (nrhs > c->gm_rhs) {
+        for (auto* p : c->gm) cudaFree(p);
+        c->dev_bytes -= c->gm.size() * (size_t)c->gm_rhs * c->Ng * 16;
+        c->gm.clear();
+        c->gm_rhs = nrhs;
+    }
+    while ((int)c->gm.size() < count) {
+        cplx<double>* p = nullptr;
+        CK(cudaMalloc(&p, (size_t)c->gm_rhs * c->Ng * 16));
+        c->dev_bytes += (size_t)c->gm_rhs * c->Ng * 16;
+        c->gm.push_back(p);
+    }
+    return HELM_OK;
+}
+
+// FP64 flexible GMRES, right preconditioned by one DDM application per
+// iteration (Remark 1), on A u = b with b on the device.  Restarts every
+// cfg.restart iterations; stops when every RHS has |b - A u| <= rtol |b|.
+int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, double rtol,
+              int maxit, helm_stats* st) {
+    const int m = c->cfg.restart;
+    const int64_t Ng = c->Ng;
+    // vectors: r/w scratch (0), V_0..V_m (1..m+1), Z_0..Z_{m-1} (m+2..2m+1)
+    TRY(ensure_gm(c, nrhs, 2 * m + 2));
+    TRY(ensure_small(c, (size_t)(m + 2) * nrhs));
+    const int nblk = (int)std::min<int64_t>(256, (Ng + 4095) / 4096);
+    cplx<double>* w = c->gm[0];
+    auto V = [&](int i) { return c->gm[1 + i]; };
+    auto Z = [&](int i) { return c->gm[m + 2 + i]; };
+    std::vector<double> bn(nrhs), res(nrhs, 1.0);
+    std::vector<cplx<double>> hd((size_t)(m + 2) * nrhs);
+    std::vector<double> sc(nrhs);
+    auto norms = [&](const cplx<double>* v, std::vector<double>& out) -> int {
+        launch_dots(v, 0, 1, v, Ng, nrhs, c->small_d, c->partial_d, nblk, c->stream);
+        CK(cudaMemcpyAsync(hd.data(), c->small_d, nrhs * 16, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (int r = 0; r < nrhs; ++r) out[r] = std::sqrt(std::max(0.0, hd[r].re));
+        return HELM_OK;
+    };
+    CK(cudaMemsetAsync(x, 0, (size_t)nrhs * Ng * 16, c->stream));
+    TRY(norms(b, bn));
+    for (auto& v : bn)
+        if (v == 0) v = 1;
+    int total = 0, apps = 0;
+    double maxres = 0;
+    bool conv = false;
+    while (true) {
+        launch_apply_A(c->P, c->gwin, c->m64, b, x, w, nrhs, c->stream);
+        std::vector<double> beta(nrhs);
+        TRY(norms(w, beta));
+        maxres = 0;
+        for (int r = 0; r < nrhs; ++r) {
+            res[r] = beta[r] / bn[r];
+            maxres = std::max(maxres, res[r]);
+        }
+        if (c->cfg.verbose) fprintf(stderr, "[helm] gmres it %d max rel resid %.3e\n", total, maxres);
+        if (maxres <= rtol) {
+            conv = true;
+            break;
+        }
+        if (total >= maxit) break;
+        for (int r = 0; r < nrhs; ++r) sc[r] = beta[r] > 0 ? 1.0 / beta[r] : 0.0;
+        CK(cudaMemcpyAsync(c->scal_d, sc.data(), nrhs * 8, cudaMemcpyHostToDevice, c->stream));
+        launch_scale_vec(V(0), w, c->scal_d, Ng, nrhs, c->stream);
+        // per-RHS Hessenberg (column-major, (m+1) x m), Givens, residual vector g
+        std::vector<std::vector<cd>> H(nrhs, std::vector<cd>((size_t)(m + 1) * m, 0.0));
+        std::vector<std::vector<double>> cs(nrhs, std::vector<double>(m, 0));
+        std::vector<std::vector<cd>> sn(nrhs, std::vector<cd>(m, 0.0));
+        std::vector<std::vector<cd>> g(nrhs, std::vector<cd>(m + 1, 0.0));
+        std::vector<int> kc(nrhs, 0);
+        std::vector<char> done(nrhs, 0);
+        for (int r = 0; r < nrhs; ++r) {
+            g[r][0] = beta[r];
+            if (res[r] <= rtol) done[r] = 1;
+        }
+        int k = 0;
+        for (; k < m && total < maxit; ++k) {
+            TRY(apply_ddm_dev(c, nrhs, V(k), Z(k)));
+            ++apps;
+            // w = -A z_k (apply_A with no b); CGS2 on w: h = V^H w, w -= V h, twice.
+            // Then A z_k = sum_i (-h_i) v_i + |w| v_{k+1} with v_{k+1} = -w/|w|.
+            launch_apply_A(c->P, c->gwin, c->m64, nullptr, Z(k), w, nrhs, c->stream);
+            std::vector<std::vector<cd>> hsum(nrhs, std::vector<cd>(k + 2, 0.0));
+            for (int pass = 0; pass < 2; ++pass) {
+                for (int i = 0; i <= k; ++i)
+                    launch_dots(V(i), 0, 1, w, Ng, nrhs, c->small_d + (size_t)i * nrhs,
+                                c->partial_d, nblk, c->stream);
+                CK(cudaMemcpyAsync(hd.data(), c->small_d, (size_t)(k + 1) * nrhs * 16,
+                                   cudaMemcpyDeviceToHost, c->stream));
+                CK(cudaStreamSynchronize(c->stream));
+                for (int i = 0; i <= k; ++i)
+                    for (int r = 0; r < nrhs; ++r)
+                        hsum[r][i] += cd(hd[(size_t)i * nrhs + r].re, hd[(size_t)i * nrhs + r].im);
+                for (int i = 0; i <= k; ++i)
+                    launch_sub_combo(w, V(i), 0, 1, c->small_d + (size_t)i * nrhs, Ng, nrhs, -1.0,
+                                     c->stream);
+            }
+            std::vector<double> wn(nrhs);
+            TRY(norms(w, wn));
+            for (int r = 0; r < nrhs; ++r) sc[r] = wn[r] > 1e-300 ? -1.0 / wn[r] : 0.0;
+            CK(cudaMemcpyAsync(c->scal_d, sc.data(), nrhs * 8, cudaMemcpyHostToDevice, c->stream));
+            launch_scale_vec(V(k + 1), w, c->scal_d, Ng, nrhs, c->stream);
+            ++total;
+            bool all = true;
+            maxres = 0;
+            for (int r = 0; r < nrhs; ++r) {
+                if (done[r]) continue;
+                std::vector<cd>& Hr = H[r];
+                for (int i = 0; i <= k; ++i) Hr[(size_t)k * (m + 1) + i] = -hsum[r][i];
+                Hr[(size_t)k * (m + 1) + k + 1] = wn[r];
+                for (int i = 0; i < k; ++i) {
+                    cd a = Hr[(size_t)k * (m + 1) + i], bb = Hr[(size_t)k * (m + 1) + i + 1];
+                    Hr[(size_t)k * (m + 1) + i] = cs[r][i] * a + sn[r][i] * bb;
+                    Hr[(size_t)k * (m + 1) + i + 1] = -std::conj(sn[r][i]) * a + cs[r][i] * bb;
+                }
+                cd a = Hr[(size_t)k * (m + 1) + k], bb = Hr[(size_t)k * (m + 1) + k + 1];
+                double t = std::sqrt(std::norm(a) + std::norm(bb));
+                if (std::abs(a) == 0) {
+                    cs[r][k] = 0;
+                    sn[r][k] = 1;
+                    Hr[(size_t)k * (m + 1) + k] = bb;
+                } else {
+                    cs[r][k] = std::abs(a) / t;
+                    sn[r][k] = (a / std::abs(a)) * std::conj(bb) / t;
+                    Hr[(size_t)k * (m + 1) + k] = (a / std::abs(a)) * t;
+                }
+                Hr[(size_t)k * (m + 1) + k + 1] = 0;
+                g[r][k + 1] = -std::conj(sn[r][k]) * g[r][k];
+                g[r][k] = cs[r][k] * g[r][k];
+                kc[r] = k + 1;
+                double est = std::abs(g[r][k + 1]) / bn[r];
+                res[r] = est;
+                if (est <= rtol) done[r] = 1;
+                maxres = std::max(maxres, est);
+                all = all && done[r];
+            }
+            if (c->cfg.verbose) fprintf(stderr, "[helm]   inner %d est %.3e\n", total, maxres);
+            if (all) {
+                ++k;
+                break;
+            }
+        }
+        // y = R^{-1} g per RHS, then x += sum_i y_i Z_i
+        std::vector<cplx<double>> coef((size_t)k * nrhs, {0, 0});
+        for (int r = 0; r < nrhs; ++r) {
+            int kk = kc[r];
+            std::vector<cd> y(kk, 0.0);
+            for (int i = kk - 1; i >= 0; --i) {
+                cd s = g[r][i];
+                for (int j2 = i + 1; j2 < kk; ++j2) s -= H[r][(size_t)j2 * (m + 1) + i] * y[j2];
+                y[i] = s / H[r][(size_t)i * (m + 1) + i];
+            }
+            for (int i = 0; i < kk; ++i) coef[(size_t)i * nrhs + r] = {y[i].real(), y[i].imag()};
+        }
+        CK(cudaMemcpyAsync(c->small_d, coef.data(), coef.size() * 16, cudaMemcpyHostToDevice,
+                           c->stream));
+        for (int i = 0; i < k; ++i)
+            launch_sub_combo(x, Z(i), 0, 1, c->small_d + (size_t)i * nrhs, Ng, nrhs, 1.0, c->stream);
+        CK(cudaStreamSynchronize(c->stream));
+    }
+    if (st) {
+        st->iters = total;
+        st->applications = apps;
+        st->resid = maxres;
+        st->levels = (int)c->levels.size();
+        st->solves = c->nsolves;
+    }
+    CK(cudaGetLastError());
+    if (!conv) return fail(HELM_ERR_NO_CONVERGENCE, "GMRES reached maxit");
+    return HELM_OK;
+}
+
+double now_ms() {
+    return std::chrono::duration<double, std::milli>(
+               std::chrono::steady_clock::now().time_since_epoch())
+        .count();
+}
+
+}  // namespace
+
+// ============================================================================= C ABI
+extern "C" {
+
+int helm_setup(helm_ctx** out, int ndim, const int64_t n[3], double h, double omega,
+               const double* m, const helm_pml* pml, const helm_partition* part,
+               const helm_config* cfg) {
+    if (!out) return fail(HELM_ERR_ARG, "out is null");
+    *out = nullptr;
+    helm_ctx* c = new helm_ctx();
+    int rc = setup_impl(c, ndim, n, h, omega, m, pml, part, cfg);
+    if (rc != HELM_OK) {
+        std::string keep = g_last_error;
+        helm_destroy(c);
+        g_last_error = keep;
+        return rc;
+    }
+    *out = c;
+    return HELM_OK;
+}
+
+int helm_factor(helm_ctx* c) {
+    if (!c) return fail(HELM_ERR_ARG, "null context");
+    if (c->factored) return HELM_OK;
+    double t0 = now_ms();
+    if (!c->fac) {
+        CK(cudaMalloc(&c->fac, c->fac_bytes));
+        c->dev_bytes += c->fac_bytes;
+    }
+    CK(cudaMemsetAsync(c->fac, 0, c->fac_bytes, c->stream));
+    CK(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream));
+    if (c->prec == HELM_PREC_F64)
+        launch_factor_f64(c->subs_d, c->P.nsub, c->nbp_max, c->P, c->m64, c->an64, c->af64,
+                          static_cast<double*>(c->fac), c->err_d, c->stream);
+    else
+        launch_factor_f32(c->subs_d, c->P.nsub, c->nbp_max, c->P, c->m32, c->an32, c->af32,
+                          static_cast<float*>(c->fac), c->err_d, c->stream);
+    CK(cudaGetLastError());
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, c->err_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (err) return fail(HELM_ERR_NUMERIC, "zero or non-finite pivot in a subdomain factor");
+    c->factored = true;
+    c->t_factor_ms = now_ms() - t0;
+    return HELM_OK;
+}
+
+int helm_apply_ddm(helm_ctx* c, int nrhs, const void* F, void* U, int mem) {
+    if (!c || !F || !U || nrhs < 1) return fail(HELM_ERR_ARG, "bad argument");
+    if (!c->factored) return fail(HELM_ERR_NOT_FACTORED, "call helm_factor first");
+    size_t bytes = (size_t)nrhs * c->Ng * 16;
+    Staged f, u;
+    TRY(stage_in(c, F, bytes, mem, f));
+    TRY(stage_in(c, mem == HELM_MEM_DEVICE ? U : nullptr, bytes, mem, u));
+    TRY(ensure_bvec(c, nrhs));
+    launch_scale_J(c->P, c->gwin, f.ptr, c->bvec, nrhs, false, c->stream);
+    TRY(apply_ddm_dev(c, nrhs, c->bvec, u.ptr));
+    return stage_out(c, U, u, bytes, mem);
+}
+
+static int solve_common(helm_ctx* c, int nrhs, const void* F, void* U, int mem, double rtol,
+                        int maxit, helm_stats* st, bool adjoint) {
+    if (!c || !F || !U || nrhs < 1 || !(rtol > 0) || maxit < 1)
+        return fail(HELM_ERR_ARG, "bad argument");
+    if (!c->factored) return fail(HELM_ERR_NOT_FACTORED, "call helm_factor first");
+    double t0 = now_ms();
+    size_t bytes = (size_t)nrhs * c->Ng * 16;
+    Staged f, u;
+    TRY(stage_in(c, F, bytes, mem, f));
+    TRY(stage_in(c, mem == HELM_MEM_DEVICE ? U : nullptr, bytes, mem, u));
+    TRY(ensure_bvec(c, nrhs));
+    if (adjoint) {
+        // A^H lam = g  <=>  A conj(lam) = conj(g)  (A^T = A)
+        CK(cudaMemcpyAsync(c->bvec, f.ptr, bytes, cudaMemcpyDeviceToDevice, c->stream));
+        launch_conj(c->bvec, (int64_t)nrhs * c->Ng, c->stream);
+    } else {
+        launch_scale_J(c->P, c->gwin, f.ptr, c->bvec, nrhs, false, c->stream);
+    }
+    int rc = gmres_dev(c, nrhs, c->bvec, u.ptr, rtol, maxit, st);
+    if (rc != HELM_OK && rc != HELM_ERR_NO_CONVERGENCE) return rc;
+    std::string msg = g_last_error;
+    if (adjoint) launch_conj(u.ptr, (int64_t)nrhs * c->Ng, c->stream);
+    TRY(stage_out(c, U, u, bytes, mem));
+    if (st) {
+        st->t_factor_ms = c->t_factor_ms;
+        st->t_solve_ms = now_ms() - t0;
+    }
+    if (rc != HELM_OK) return fail(rc, msg);
+    return HELM_OK;
+}
+
+int helm_solve(helm_ctx* c, int nrhs, const void* F, void* U, int mem, double rtol, int maxit,
+               helm_stats* st) {
+    return solve_common(c, nrhs, F, U, mem, rtol, maxit, st, false);
+}
+
+int helm_adjoint(helm_ctx* c, int nrhs, const void* G, void* L, int mem, double rtol, int maxit,
+                 helm_stats* st) {
+    return solve_common(c, nrhs, G, L, mem, rtol, maxit, st, true);
+}
+
+int helm_gradient(helm_ctx* c, int nsrc, const void* U, const void* L, double* grad, int mem) {
+    if (!c || !U || !L || !grad || nsrc < 1) return fail(HELM_ERR_ARG, "bad argument");
+    size_t bytes = (size_t)nsrc * c->Ng * 16;
+    Staged u, l;
+    TRY(stage_in(c, U, bytes, mem, u));
+    TRY(stage_in(c, L, bytes, mem, l));
+    double* gd = grad;
+    bool own = false;
+    if (mem == HELM_MEM_HOST) {
+        CK(cudaMalloc(&gd, c->Ng * 8));
+        own = true;
+    }
+    launch_gradient(c->P, c->gwin, u.ptr, l.ptr, nsrc, gd, c->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && own) e = cudaMemcpyAsync(grad, gd, c->Ng * 8, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (own) cudaFree(gd);
+    if (e != cudaSuccess) return fail(HELM_ERR_CUDA, cudaGetErrorString(e));
+    return HELM_OK;
+}
+
+int helm_residual(helm_ctx* c, int nrhs, const void* F, const void* U, void* R, int mem) {
+    if (!c || !F || !U || !R || nrhs < 1) return fail(HELM_ERR_ARG, "bad argument");
+    size_t bytes = (size_t)nrhs * c->Ng * 16;
+    Staged f, u, r;
+    TRY(stage_in(c, F, bytes, mem, f));
+    TRY(stage_in(c, U, bytes, mem, u));
+    TRY(stage_in(c, mem == HELM_MEM_DEVICE ? R : nullptr, bytes, mem, r));
+    TRY(ensure_bvec(c, nrhs));
+    launch_scale_J(c->P, c->gwin, f.ptr, c->bvec, nrhs, false, c->stream);
+    launch_apply_A(c->P, c->gwin, c->m64, c->bvec, u.ptr, r.ptr, nrhs, c->stream);
+    CK(cudaGetLastError());
+    return stage_out(c, R, r, bytes, mem);
+}
+
+int helm_subdomain_solve(helm_ctx* c, int s, int nrhs, const void* R, void* U, int mem) {
+    if (!c || !R || !U || nrhs < 1 || s < 0 || s >= c->P.nsub) return fail(HELM_ERR_ARG, "bad argument");
+    if (!c->factored) return fail(HELM_ERR_NOT_FACTORED, "call helm_factor first");
+    const SubDesc& S = c->subs_h[s];
+    const int64_t we = S.win_elems;
+    size_t bytes = (size_t)nrhs * we * 16;
+    Staged r;
+    TRY(stage_in(c, R, bytes, mem, r));
+    // a private buffer [rhs][window] in the working precision
+    void* wb = nullptr;
+    CK(cudaMalloc(&wb, (size_t)nrhs * we * elem_size(c)));
+    std::vector<cplx<double>> host((size_t)nrhs * we);
+    CK(cudaMemcpyAsync(host.data(), r.ptr, bytes, cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->prec == HELM_PREC_F64) {
+        CK(cudaMemcpy(wb, host.data(), bytes, cudaMemcpyHostToDevice));
+    } else {
+        std::vector<cplx<float>> h32(host.size());
+        for (size_t i = 0; i < host.size(); ++i) h32[i] = {(float)host[i].re, (float)host[i].im};
+        CK(cudaMemcpy(wb, h32.data(), h32.size() * 8, cudaMemcpyHostToDevice));
+    }
+    Task t{0, s, 0, 0, 0};
+    Task* td = nullptr;
+    CK(cudaMalloc(&td, sizeof(Task)));
+    CK(cudaMemcpy(td, &t, sizeof(Task), cudaMemcpyHostToDevice));
+    const int panel = auto_panel(c, nrhs);
+    if (c->prec == HELM_PREC_F64)
+        launch_solve<double>(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
+                             static_cast<const double*>(c->fac), c->Pv64, c->inva64,
+                             static_cast<cplx<double>*>(wb), we, c->stream);
+    else
+        launch_solve<float>(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
+                            static_cast<const float*>(c->fac), c->Pv32, c->inva32,
+                            static_cast<cplx<float>*>(wb), we, c->stream);
+    CK(cudaGetLastError());
+    CK(cudaStreamSynchronize(c->stream));
+    if (c->prec == HELM_PREC_F64) {
+        CK(cudaMemcpy(host.data(), wb, bytes, cudaMemcpyDeviceToHost));
+    } else {
+        std::vector<cplx<float>> h32(host.size());
+        CK(cudaMemcpy(h32.data(), wb, h32.size() * 8, cudaMemcpyDeviceToHost));
+        for (size_t i = 0; i < host.size(); ++i) host[i] = {h32[i].re, h32[i].im};
+    }
+    cudaFree(wb);
+    cudaFree(td);
+    if (mem == HELM_MEM_HOST)
+        std::memcpy(U, host.data(), bytes);
+    else
+        CK(cudaMemcpy(U, host.data(), bytes, cudaMemcpyHostToDevice));
+    return HELM_OK;
+}
+
+int helm_window_info(helm_ctx* c, int s, int64_t lo[3], int64_t hi[3]) {
+    if (!c || s < 0 || s >= c->P.nsub || !lo || !hi) return fail(HELM_ERR_ARG, "bad argument");
+    for (int a = 0; a < 3; ++a) {
+        lo[a] = c->subs_h[s].lo[a];
+        hi[a] = c->subs_h[s].hi[a];
+    }
+    return HELM_OK;
+}
+
+int helm_problem_info(helm_ctx* c, int64_t* nsub, int64_t N[3]) {
+    if (!c) return fail(HELM_ERR_ARG, "null context");
+    if (nsub) *nsub = c->P.nsub;
+    if (N)
+        for (int a = 0; a < 3; ++a) N[a] = c->P.N[a];
+    return HELM_OK;
+}
+
+int64_t helm_device_bytes(helm_ctx* c) { return c ? (int64_t)c->dev_bytes : 0; }
+
+void helm_destroy(helm_ctx* c) {
+    if (!c) return;
+    void* ptrs[] = {c->subs_d, c->g_alpha, c->m64, c->m32, c->an64, c->af64, c->an32, c->af32,
+                    c->Pv64, c->inva64, c->Pv32, c->inva32, c->tab64, c->tab32, c->box_of,
+                    c->fac, c->err_d, c->tasks_d, c->inc_d, c->node_buf_d, c->buf, c->bvec,
+                    c->small_d, c->partial_d, c->scal_d};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    for (auto* p : c->gm) cudaFree(p);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    delete c;
+}
+
+const char* helm_strerror(int code) {
+    switch (code) {
+        case HELM_OK: return "ok";
+        case HELM_ERR_ARG: return "invalid argument";
+        case HELM_ERR_OOM: return "out of device memory";
+        case HELM_ERR_NOT_FACTORED: return "not factored";
+        case HELM_ERR_NO_CONVERGENCE: return "GMRES did not converge";
+        case HELM_ERR_TIMEOUT: return "device wait timed out";
+        case HELM_ERR_CUDA: return "CUDA error";
+        case HELM_ERR_NUMERIC: return "numerical breakdown in a factor";
+        default: return "unknown error";
+    }
+}
+
+const char* helm_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

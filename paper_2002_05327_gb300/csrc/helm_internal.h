@@ -1,0 +1,190 @@
+// Internal types shared by the libhelm translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/helm.h"
+
+namespace helm {
+
+// ----------------------------------------------------------------------------- complex
+template <typename T>
+struct cplx {
+    T re, im;
+};
+template <typename T> struct vec2;
+template <> struct vec2<float> { using type = float2; };
+template <> struct vec2<double> { using type = double2; };
+
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> mk(T r, T i) { return cplx<T>{r, i}; }
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> operator+(cplx<T> a, cplx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> operator-(cplx<T> a, cplx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> operator*(cplx<T> a, cplx<T> b) {
+    return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> operator*(T s, cplx<T> a) { return {s * a.re, s * a.im}; }
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> cneg(cplx<T> a) { return {-a.re, -a.im}; }
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> cconj(cplx<T> a) { return {a.re, -a.im}; }
+template <typename T>
+__host__ __device__ __forceinline__ T cabs2(cplx<T> a) { return a.re * a.re + a.im * a.im; }
+template <typename T>
+__host__ __device__ __forceinline__ cplx<T> cinv(cplx<T> a) {
+    T s = T(1) / (a.re * a.re + a.im * a.im);
+    return {a.re * s, -a.im * s};
+}
+// acc += a * b
+template <typename T>
+__host__ __device__ __forceinline__ void cfma(cplx<T>& acc, cplx<T> a, cplx<T> b) {
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+}
+template <typename T, typename U>
+__host__ __device__ __forceinline__ cplx<T> ccast(cplx<U> a) { return {T(a.re), T(a.im)}; }
+
+// ----------------------------------------------------------------------------- window
+// A box-shaped window of the full grid with its own PML coefficients: the
+// global problem (lo = 0, n = N) or one subdomain problem P_{Omega_ij}.
+// alpha_node[a][i] = alpha_a at node lo[a]+i, alpha_face[a][i] = alpha_a at the
+// face between nodes lo[a]+i-1 and lo[a]+i (i = 0..n[a]).
+template <typename T>
+struct Win {
+    int lo[3];
+    int n[3];
+    const cplx<T>* alpha_node[3];
+    const cplx<T>* alpha_face[3];
+};
+
+// The 2*ndim+1 coefficients of row k of the J-multiplied PML operator:
+// (A u)_k = diag u_k + sum_a cp[a] u_{k+e_a} + cm[a] u_{k-e_a}
+//   cp[a] = prod_{b!=a} alpha_b(node) / (h^2 alpha_a(face k_a+1/2)),
+//   cm[a] likewise with the face k_a-1/2,
+//   diag  = omega^2 m J - sum_a (cp[a] + cm[a]),  J = prod_b alpha_b(node).
+template <typename T>
+struct Stencil {
+    cplx<T> diag;
+    cplx<T> cp[3], cm[3];
+};
+
+template <typename T>
+__device__ __forceinline__ Stencil<T> stencil_at(const Win<T>& w, int ndim, const int x[3],
+                                                 T inv_h2, T omega2, T m) {
+    cplx<T> an[3];
+    for (int a = 0; a < 3; ++a) an[a] = (a < ndim) ? w.alpha_node[a][x[a]] : mk<T>(1, 0);
+    Stencil<T> s;
+    cplx<T> J = an[0] * an[1] * an[2];
+    cplx<T> sum = mk<T>(0, 0);
+    for (int a = 0; a < 3; ++a) {
+        if (a >= ndim) {
+            s.cp[a] = s.cm[a] = mk<T>(0, 0);
+            continue;
+        }
+        cplx<T> P = mk<T>(inv_h2, 0);
+        for (int b = 0; b < ndim; ++b)
+            if (b != a) P = P * an[b];
+        s.cp[a] = P * cinv(w.alpha_face[a][x[a] + 1]);
+        s.cm[a] = P * cinv(w.alpha_face[a][x[a]]);
+        sum = sum + s.cp[a] + s.cm[a];
+    }
+    s.diag = (omega2 * m) * J - sum;
+    return s;
+}
+
+// ----------------------------------------------------------------------------- subdomains
+struct SubDesc {
+    int lo[3], hi[3];          // window node range (global, hi exclusive)
+    int box_lo[3], box_hi[3];  // box node range (global)
+    int nw[3];                 // window sizes (nw[2] = 1 in 2D)
+    int ib[3];                 // box index per axis
+    int nblk;                  // nodes per block (line in 2D, plane in 3D)
+    int nbp;                   // nblk padded to a multiple of 32
+    int nlines;                // blocks (window extent along the slowest axis)
+    int64_t alpha_off[3];      // offset of this window's node alphas per axis
+    int64_t face_off[3];       // offset of this window's face alphas per axis
+    int64_t fac_off;           // offset (elements of T) of this subdomain's factors
+    int64_t coup_off;          // offset of Pv (nblk) in the coupling arrays
+    int64_t inva_off;          // offset of 1/alpha_slow(face) (nlines+1)
+    int64_t win_elems;         // nodes in the window
+};
+
+// One (sweep, subdomain) solve of a dependency level, with its incoming
+// transferred sources [in_off, in_off + in_cnt).
+struct Task {
+    int sweep;
+    int sub;
+    int in_off, in_cnt;
+    int64_t buf_off;  // element offset (complex) of this node's window buffer per RHS block
+};
+
+// Incoming transferred source: Psi_{dir; sender}(u^{l_src}_{sender}).
+struct Incoming {
+    int dir[3];
+    int sender;
+    int64_t sender_buf_off;
+};
+
+// ----------------------------------------------------------------------------- kernels
+struct DevProblem {
+    int ndim;
+    int N[3];
+    int d;                  // overlap cells
+    int nsub;
+    int nb[3];
+    double h, omega;
+};
+
+void launch_factor_f32(const SubDesc* subs, int nsub, int nbp_max, const DevProblem& P,
+                       const float* m32, const cplx<float>* an, const cplx<float>* af,
+                       float* fac, int* err, cudaStream_t st);
+void launch_factor_f64(const SubDesc* subs, int nsub, int nbp_max, const DevProblem& P,
+                       const double* m64, const cplx<double>* an, const cplx<double>* af,
+                       double* fac, int* err, cudaStream_t st);
+
+template <typename T>
+void launch_solve(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
+                  int panel, const T* fac, const cplx<T>* Pv, const cplx<T>* inva, cplx<T>* buf,
+                  int64_t buf_rhs_stride, cudaStream_t st);
+
+template <typename T>
+void launch_gather(const Task* tasks, int ntask, int64_t max_win, const SubDesc* subs,
+                   const Incoming* inc, const DevProblem& P, const T* m, const cplx<T>* an,
+                   const cplx<T>* af, const T* beta_tab, const cplx<double>* b, int nrhs,
+                   cplx<T>* buf, int64_t buf_rhs_stride, cudaStream_t st);
+
+template <typename T>
+void launch_assemble(const DevProblem& P, const SubDesc* subs, const int* box_of,
+                     const int64_t* node_buf, int nsweeps, const T* beta_tab,
+                     const cplx<T>* buf, int64_t buf_rhs_stride, int nrhs, cplx<double>* U,
+                     cudaStream_t st);
+
+// global FP64 kernels
+void launch_scale_J(const DevProblem& P, const Win<double>& g, const cplx<double>* f,
+                    cplx<double>* b, int nrhs, bool conj_in, cudaStream_t st);
+void launch_apply_A(const DevProblem& P, const Win<double>& g, const double* m,
+                    const cplx<double>* b, const cplx<double>* u, cplx<double>* r, int nrhs,
+                    cudaStream_t st);  // r = b - A u (b may be null: r = -A u)
+void launch_dots(const cplx<double>* V, int64_t vstride, int nv, const cplx<double>* w,
+                 int64_t n, int nrhs, cplx<double>* out, cplx<double>* partial, int nblk,
+                 cudaStream_t st);  // out[i*nrhs+c] = <V_i[c], w[c]>
+void launch_sub_combo(cplx<double>* w, const cplx<double>* V, int64_t vstride, int nv,
+                      const cplx<double>* coef, int64_t n, int nrhs, double sign,
+                      cudaStream_t st);  // w[c] += sign * sum_i coef[i*nrhs+c] V_i[c]
+void launch_scale_vec(cplx<double>* v, const cplx<double>* src, const double* s, int64_t n,
+                      int nrhs, cudaStream_t st);  // v[c] = src[c] * s[c]
+void launch_conj(cplx<double>* v, int64_t count, cudaStream_t st);
+void launch_gradient(const DevProblem& P, const Win<double>& g, const cplx<double>* U,
+                     const cplx<double>* L, int nsrc, double* grad, cudaStream_t st);
+
+}  // namespace helm

@@ -1,0 +1,194 @@
+// Global FP64 kernels: J scaling of sources, the residual b - A u of the
+// global PML system (Eq. 2.2, J-multiplied 5/7-point form), the batched
+// BLAS-1 of GMRES (one Krylov space per right-hand side) and the gradient of
+// the receiver misfit with respect to m.
+//
+// Reductions are deterministic: every block reduces a fixed contiguous chunk
+// with a fixed tree, and a second pass sums the block partials in order.
+#include "helm_internal.h"
+
+namespace helm {
+
+__device__ __forceinline__ void unflat(int64_t k, const int N[3], int g[3]) {
+    g[0] = (int)(k % N[0]);
+    g[1] = (int)((k / N[0]) % N[1]);
+    g[2] = (int)(k / ((int64_t)N[0] * N[1]));
+}
+
+__global__ void scale_J_kernel(DevProblem P, Win<double> w, const cplx<double>* f,
+                               cplx<double>* b, int nrhs, int conj_in) {
+    const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (k >= Ng) return;
+    int g[3];
+    unflat(k, P.N, g);
+    cplx<double> J = mk<double>(1, 0);
+    for (int a = 0; a < P.ndim; ++a) J = J * w.alpha_node[a][g[a]];
+    cplx<double> v = f[(int64_t)c * Ng + k];
+    if (conj_in) v = cconj(v);
+    b[(int64_t)c * Ng + k] = J * v;
+}
+
+void launch_scale_J(const DevProblem& P, const Win<double>& g, const cplx<double>* f,
+                    cplx<double>* b, int nrhs, bool conj_in, cudaStream_t st) {
+    const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
+    dim3 grid((unsigned)((Ng + 255) / 256), nrhs);
+    scale_J_kernel<<<grid, 256, 0, st>>>(P, g, f, b, nrhs, conj_in ? 1 : 0);
+}
+
+__global__ void apply_A_kernel(DevProblem P, Win<double> w, const double* __restrict__ m,
+                               const cplx<double>* __restrict__ b,
+                               const cplx<double>* __restrict__ u, cplx<double>* r) {
+    const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (k >= Ng) return;
+    int g[3];
+    unflat(k, P.N, g);
+    Stencil<double> st = stencil_at(w, P.ndim, g, 1.0 / (P.h * P.h), P.omega * P.omega, m[k]);
+    const cplx<double>* uc = u + (int64_t)c * Ng;
+    cplx<double> Au = st.diag * uc[k];
+    int64_t stride = 1;
+    for (int a = 0; a < P.ndim; ++a) {
+        if (g[a] + 1 < P.N[a]) Au = Au + st.cp[a] * uc[k + stride];
+        if (g[a] > 0) Au = Au + st.cm[a] * uc[k - stride];
+        stride *= P.N[a];
+    }
+    cplx<double> out = cneg(Au);
+    if (b) out = out + b[(int64_t)c * Ng + k];
+    r[(int64_t)c * Ng + k] = out;
+}
+
+void launch_apply_A(const DevProblem& P, const Win<double>& g, const double* m,
+                    const cplx<double>* b, const cplx<double>* u, cplx<double>* r, int nrhs,
+                    cudaStream_t st) {
+    const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
+    dim3 grid((unsigned)((Ng + 255) / 256), nrhs);
+    apply_A_kernel<<<grid, 256, 0, st>>>(P, g, m, b, u, r);
+}
+
+// ---- batched dots: out[i*nrhs + c] = sum_k conj(V_i[c][k]) w[c][k]
+constexpr int DOT_NT = 256;
+
+__global__ void dots_partial_kernel(const cplx<double>* __restrict__ V, int64_t vstride,
+                                    const cplx<double>* __restrict__ w, int64_t n, int nrhs,
+                                    cplx<double>* partial, int nblk) {
+    __shared__ double sr[DOT_NT], si[DOT_NT];
+    const int blk = blockIdx.x;
+    const int i = blockIdx.y / nrhs, c = blockIdx.y % nrhs;
+    const int64_t chunk = (n + nblk - 1) / nblk;
+    const int64_t k0 = (int64_t)blk * chunk;
+    const int64_t k1 = min(n, k0 + chunk);
+    const cplx<double>* vi = V + (int64_t)i * vstride + (int64_t)c * n;
+    const cplx<double>* wc = w + (int64_t)c * n;
+    double ar = 0, ai = 0;
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += DOT_NT) {
+        cplx<double> a = vi[k], b = wc[k];
+        ar += a.re * b.re + a.im * b.im;
+        ai += a.re * b.im - a.im * b.re;
+    }
+    sr[threadIdx.x] = ar;
+    si[threadIdx.x] = ai;
+    __syncthreads();
+    for (int s = DOT_NT / 2; s > 0; s >>= 1) {
+        if (threadIdx.x < s) {
+            sr[threadIdx.x] += sr[threadIdx.x + s];
+            si[threadIdx.x] += si[threadIdx.x + s];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * nblk + blk] = mk<double>(sr[0], si[0]);
+}
+
+__global__ void dots_final_kernel(const cplx<double>* partial, int nblk, int count,
+                                  cplx<double>* out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= count) return;
+    double r = 0, i = 0;
+    for (int b = 0; b < nblk; ++b) {
+        r += partial[(int64_t)t * nblk + b].re;
+        i += partial[(int64_t)t * nblk + b].im;
+    }
+    out[t] = mk<double>(r, i);
+}
+
+void launch_dots(const cplx<double>* V, int64_t vstride, int nv, const cplx<double>* w,
+                 int64_t n, int nrhs, cplx<double>* out, cplx<double>* partial, int nblk,
+                 cudaStream_t st) {
+    dim3 grid(nblk, nv * nrhs);
+    dots_partial_kernel<<<grid, DOT_NT, 0, st>>>(V, vstride, w, n, nrhs, partial, nblk);
+    int count = nv * nrhs;
+    dots_final_kernel<<<(count + 127) / 128, 128, 0, st>>>(partial, nblk, count, out);
+}
+
+// w[c] += sign * sum_i coef[i*nrhs+c] V_i[c]
+__global__ void sub_combo_kernel(cplx<double>* w, const cplx<double>* __restrict__ V,
+                                 int64_t vstride, int nv, const cplx<double>* __restrict__ coef,
+                                 int64_t n, int nrhs, double sign) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (k >= n) return;
+    cplx<double> acc = w[(int64_t)c * n + k];
+    for (int i = 0; i < nv; ++i) {
+        cplx<double> a = coef[i * nrhs + c];
+        cplx<double> v = V[(int64_t)i * vstride + (int64_t)c * n + k];
+        acc = acc + sign * (a * v);
+    }
+    w[(int64_t)c * n + k] = acc;
+}
+
+void launch_sub_combo(cplx<double>* w, const cplx<double>* V, int64_t vstride, int nv,
+                      const cplx<double>* coef, int64_t n, int nrhs, double sign,
+                      cudaStream_t st) {
+    dim3 grid((unsigned)((n + 255) / 256), nrhs);
+    sub_combo_kernel<<<grid, 256, 0, st>>>(w, V, vstride, nv, coef, n, nrhs, sign);
+}
+
+__global__ void scale_vec_kernel(cplx<double>* v, const cplx<double>* src, const double* s,
+                                 int64_t n) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (k >= n) return;
+    v[(int64_t)c * n + k] = s[c] * src[(int64_t)c * n + k];
+}
+
+void launch_scale_vec(cplx<double>* v, const cplx<double>* src, const double* s, int64_t n,
+                      int nrhs, cudaStream_t st) {
+    dim3 grid((unsigned)((n + 255) / 256), nrhs);
+    scale_vec_kernel<<<grid, 256, 0, st>>>(v, src, s, n);
+}
+
+__global__ void conj_kernel(cplx<double>* v, int64_t count) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < count) v[k].im = -v[k].im;
+}
+
+void launch_conj(cplx<double>* v, int64_t count, cudaStream_t st) {
+    conj_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(v, count);
+}
+
+__global__ void gradient_kernel(DevProblem P, Win<double> w, const cplx<double>* __restrict__ U,
+                                const cplx<double>* __restrict__ L, int nsrc, double* grad) {
+    const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Ng) return;
+    int g[3];
+    unflat(k, P.N, g);
+    cplx<double> J = mk<double>(1, 0);
+    for (int a = 0; a < P.ndim; ++a) J = J * w.alpha_node[a][g[a]];
+    double acc = 0;
+    for (int s = 0; s < nsrc; ++s) {
+        cplx<double> t = cconj(L[(int64_t)s * Ng + k]) * (J * U[(int64_t)s * Ng + k]);
+        acc += t.re;
+    }
+    grad[k] = -P.omega * P.omega * acc;
+}
+
+void launch_gradient(const DevProblem& P, const Win<double>& g, const cplx<double>* U,
+                     const cplx<double>* L, int nsrc, double* grad, cudaStream_t st) {
+    const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
+    gradient_kernel<<<(unsigned)((Ng + 255) / 256), 256, 0, st>>>(P, g, U, L, nsrc, grad);
+}
+
+}  // namespace helm

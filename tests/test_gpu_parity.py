@@ -1,0 +1,188 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (relative L2 over the whole output):
+  * FP64 path (HELM_PREC_F64): 1e-10.  Both sides solve the same complex128
+    systems; only the elimination order differs (block Gauss-Jordan vs sparse
+    LU), so the gap is rounding amplified by the local condition numbers.
+  * Mixed path (HELM_PREC_MIXED), raw DDM: 1e-3.  complex64 factors carry a
+    unit roundoff of 6e-8; the block recurrence over ~50-200 lines and the
+    explicit inverses amplify it by the local condition numbers (~1e2-1e3 on
+    these PML blocks).
+  * After FP64 GMRES (the product's answer): 1e-6 against the global direct
+    solve, the bound the method promises after refinement.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import adjoint as OA
+from oracle import ddm as OD
+from oracle import helmholtz as OH
+
+pytestmark = pytest.mark.gpu
+
+TOL = {0: 1e-10, 1: 1e-3}
+
+
+@pytest.fixture(scope="module")
+def H():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2002_05327_gb300 as H
+    from paper_2002_05327_gb300.build import build
+    build()
+    return H
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _ctx(H, wl, prec, **kw):
+    c = H.helm_setup_workload(wl, precision=prec, **kw)
+    H.helm_factor(c)
+    return c
+
+
+CASES = {
+    "2d-layered-3x2": lambda: W.small_2d(),
+    "2d-layered-4x3-5rhs": lambda: W.small_2d(nx=60, ny=52, nbx=4, nby=3, nrhs=5),
+    "2d-1x1": lambda: W.small_2d(nx=30, ny=26, nbx=1, nby=1, nrhs=1),
+    "2d-strip-3x1": lambda: W.small_2d(nx=45, ny=20, nbx=3, nby=1, nrhs=2),
+    "3d-const-2x2x2": lambda: W.small_3d(),
+    "3d-layered-3x2x2": lambda: W.small_3d(n=(27, 18, 16), nb=(3, 2, 2), nrhs=1, medium="layered"),
+}
+
+
+def _nonuniform():
+    wl = W.small_2d(nx=64, ny=50, nbx=3, nby=3, nrhs=3)
+    cuts = (np.array([0, 17, 40, 64]), np.array([0, 21, 33, 50]))
+    return dataclasses.replace(wl, cuts=cuts)
+
+
+CASES["2d-nonuniform-3x3"] = _nonuniform
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("case", sorted(CASES))
+def test_apply_ddm_matches_algorithm(H, case, prec):
+    """helm_apply_ddm equals the oracle's Algorithm 3.1 / 4.1 (same windows,
+    cutoffs, routing) element by element."""
+    wl = CASES[case]()
+    ctx = _ctx(H, wl, prec)
+    u = H.helm_apply_ddm(ctx, wl.f)
+    ref = OD.ddm_solution(wl)
+    assert rel(u, ref) < TOL[prec], rel(u, ref)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_subdomain_solve_matches_local_direct_solve(H, prec):
+    wl = W.small_2d(nx=60, ny=52, nbx=4, nby=3, nrhs=3)
+    ctx = _ctx(H, wl, prec)
+    part = OD.Partition(wl)
+    rng = np.random.default_rng(1)
+    for s in (0, 5, 11):
+        I = (s % 4, s // 4)
+        sub = part.subs[I]
+        lo, hi = H.helm_window_info(ctx, s)
+        assert lo == sub.lo and hi == sub.hi
+        R = rng.standard_normal((3,) + sub.shape) + 1j * rng.standard_normal((3,) + sub.shape)
+        u = H.helm_subdomain_solve(ctx, s, R)
+        ref = part.local_solve(sub, R)
+        assert rel(u, ref) < (1e-11 if prec == 0 else 1e-4), (s, rel(u, ref))
+    ctx.close()
+
+
+def test_config1_ddm_fp64(H):
+    """Config 1 (160^2, 2x2, one Gaussian): the plain complex128 GPU DDM equals
+    the oracle's Algorithm 3.1, and both are within PML truncation of the
+    global solution."""
+    wl = W.config(1)
+    ctx = _ctx(H, wl, 0)
+    u = H.helm_apply_ddm(ctx, wl.f)
+    ref = OD.ddm_solution(wl)
+    assert rel(u, ref) < 1e-10
+    assert rel(u, OH.solve_global(wl)) < 5e-4
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_gmres_reaches_global_solution(H, prec):
+    wl = W.small_2d(nx=64, ny=56, nbx=3, nby=3, pml=10, overlap=4, sub_pml=10, nrhs=3)
+    ctx = _ctx(H, wl, prec)
+    x, st = H.helm_solve(ctx, wl.f, rtol=1e-10, maxit=60)
+    ref = OH.solve_global(wl)
+    assert rel(x, ref) < 1e-6, rel(x, ref)
+    assert st["resid"] <= 1e-10
+    ctx.close()
+
+
+def test_residual_matches_operator(H):
+    wl = W.small_3d(n=(12, 10, 9), nb=(2, 2, 1), pml=4, overlap=2, sub_pml=3, nrhs=2,
+                    medium="layered")
+    ctx = _ctx(H, wl, 0)
+    rng = np.random.default_rng(2)
+    u = rng.standard_normal(wl.f.shape) + 1j * rng.standard_normal(wl.f.shape)
+    r = H.helm_residual(ctx, wl.f, u)
+    A, J = OH.global_operator(wl)
+    nr = wl.f.shape[0]
+    ref = (wl.f.reshape(nr, -1) * J[None] - (A @ u.reshape(nr, -1).T).T).reshape(u.shape)
+    assert rel(r, ref) < 1e-13
+    ctx.close()
+
+
+def test_adjoint_and_gradient(H):
+    wl = W.small_2d(nx=40, ny=34, nbx=2, nby=2, pml=8, overlap=4, sub_pml=8, nrhs=2)
+    rec = np.array([(wl.pml + k, wl.pml + 2) for k in range(2, 38, 4)])
+    ctx = _ctx(H, wl, 1)
+    u, _ = H.helm_solve(ctx, wl.f, rtol=1e-11, maxit=80)
+    m_true = wl.m * 1.02
+    d = OA.receiver_values(OH.solve_global(dataclasses.replace(wl, m=m_true)), rec)
+    g_src = OA.adjoint_source(u, rec, d)
+    lam, _ = H.helm_adjoint(ctx, g_src, rtol=1e-11, maxit=80)
+    # the adjoint solve against the direct A^{-H}
+    A, _ = OH.global_operator(wl)
+    import scipy.sparse.linalg as spla
+    lu = spla.splu(A.tocsc())
+
+    def solve(b):
+        return lu.solve(np.ascontiguousarray(b.reshape(b.shape[0], -1).T)).T.reshape(b.shape)
+
+    lam_ref = OA.adjoint_solve(solve, g_src)
+    assert rel(lam, lam_ref) < 1e-6
+    g = H.helm_gradient(ctx, u, lam)
+    g_ref = OA.gradient(wl, u, lam)
+    assert rel(g, g_ref) < 1e-12
+    ctx.close()
+
+
+def test_errors_are_reported(H):
+    wl = W.small_2d()
+    with pytest.raises(H.HelmError) as e:
+        H.helm_setup(2, wl.n, wl.h, wl.omega, wl.m, wl.pml, wl.sigma0, (40, 1), 4)
+    assert e.value.code == H.HELM_ERR_ARG
+    ctx = H.helm_setup_workload(wl, precision=1)
+    with pytest.raises(H.HelmError) as e:
+        H.helm_apply_ddm(ctx, wl.f)
+    assert e.value.code == H.HELM_ERR_NOT_FACTORED
+    H.helm_factor(ctx)
+    with pytest.raises(H.HelmError) as e:
+        H.helm_solve(ctx, wl.f, rtol=1e-14, maxit=1)
+    assert e.value.code == H.HELM_ERR_NO_CONVERGENCE
+    ctx.close()
+
+
+def test_deterministic_and_device_pointers(H):
+    import torch
+    wl = W.small_2d(nx=60, ny=52, nbx=4, nby=3, nrhs=5)
+    ctx = _ctx(H, wl, 1)
+    u1 = H.helm_apply_ddm(ctx, wl.f)
+    u2 = H.helm_apply_ddm(ctx, wl.f)
+    assert np.array_equal(u1, u2)
+    ud = H.helm_apply_ddm(ctx, torch.from_numpy(wl.f).cuda())
+    assert np.array_equal(ud.cpu().numpy(), u1)
+    ctx.close()

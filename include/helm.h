@@ -99,6 +99,7 @@ typedef struct {
     int32_t restart;    /* GMRES restart length; 0 = 30 */
     int32_t verbose;    /* 1: per-iteration residuals on stderr */
     void *stream;       /* cudaStream_t to run on; NULL = the library's own stream */
+    int32_t profile;    /* 1: time every kernel launch with CUDA events (helm_profile_get) */
 } helm_config;
 
 typedef struct {
@@ -170,6 +171,32 @@ int helm_window_info(helm_ctx *ctx, int s, int64_t lo[3], int64_t hi[3]);
 
 /* Number of subdomains, full-grid size N[3] (N[2] = 1 in 2D). */
 int helm_problem_info(helm_ctx *ctx, int64_t *nsub, int64_t N[3]);
+
+/* Kernel classes reported by helm_profile_get. */
+enum helm_kernel_class {
+    HELM_K_FACTOR = 0,   /* block-Thomas factorisation */
+    HELM_K_SOLVE = 1,    /* subdomain forward/backward solves */
+    HELM_K_GATHER = 2,   /* local sources + transferred sources (Psi) */
+    HELM_K_ASSEMBLE = 3, /* u_DDM = sum beta_00 u */
+    HELM_K_KRYLOV = 4,   /* FP64 residual, J scaling and GMRES BLAS-1 */
+    HELM_K_NCLASS = 5
+};
+
+/* Accumulated per-class counters since the last helm_profile_reset:
+ * launches counts every kernel launch; ms is device time from CUDA events
+ * recorded on the context's stream around each launch (only when
+ * helm_config.profile = 1, else 0); bytes and flops are the algorithmic
+ * DRAM bytes and floating-point operations of those launches (factor and
+ * solve classes: dense block reads/writes and complex multiply-adds). */
+typedef struct {
+    int64_t launches[8];
+    double ms[8];
+    double bytes[8];
+    double flops[8];
+} helm_profile;
+
+int helm_profile_reset(helm_ctx *ctx);
+int helm_profile_get(helm_ctx *ctx, helm_profile *out);
 
 /* Bytes of device memory held by the context. */
 int64_t helm_device_bytes(helm_ctx *ctx);

@@ -177,13 +177,13 @@ class Partition:
             if ideal:
                 if not self.subs:
                     A, _ = global_operator(wl, form)
-                    glu = spla.splu(A.tocsc(), permc_spec="MMD_AT_PLUS_A")
+                    glu = spla.splu(A.tocsc(), permc_spec="COLAMD")
                 s.A, s.lu = A, glu
             else:
                 msl = tuple(slice(ax.lo, ax.hi) for ax in reversed(axes))
                 s.A, _ = assemble(axes, wl.m[msl], wl.h, wl.omega, wl.sigma0, wl.power, form)
                 if factor:
-                    s.lu = spla.splu(s.A.tocsc(), permc_spec="MMD_AT_PLUS_A")
+                    s.lu = spla.splu(s.A.tocsc(), permc_spec="COLAMD")
             self.subs[I] = s
 
     # -- 1-D cutoffs and truncations over a range of global node indices

@@ -144,5 +144,5 @@ def solve_global(wl, f=None, form="literal", dense=False):
     if dense:
         u = np.linalg.solve(A.toarray(), b)
     else:
-        u = spla.splu(A.tocsc(), permc_spec="MMD_AT_PLUS_A").solve(np.ascontiguousarray(b))
+        u = spla.splu(A.tocsc(), permc_spec="COLAMD").solve(np.ascontiguousarray(b))
     return u.T.reshape(f.shape)

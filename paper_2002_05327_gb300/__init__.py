@@ -46,7 +46,20 @@ class helm_partition(ctypes.Structure):
 class helm_config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rhs_panel", ctypes.c_int32),
                 ("restart", ctypes.c_int32), ("verbose", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("profile", ctypes.c_int32)]
+
+
+KERNEL_CLASSES = ("factor", "solve", "gather", "assemble", "krylov")
+
+
+class helm_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 8), ("ms", ctypes.c_double * 8),
+                ("bytes", ctypes.c_double * 8), ("flops", ctypes.c_double * 8)]
+
+    def as_dict(self):
+        return {name: {"launches": int(self.launches[i]), "ms": float(self.ms[i]),
+                       "bytes": float(self.bytes[i]), "flops": float(self.flops[i])}
+                for i, name in enumerate(KERNEL_CLASSES)}
 
 
 class helm_stats(ctypes.Structure):
@@ -87,6 +100,8 @@ _SIGS = {
     "helm_problem_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_int64)]),
     "helm_device_bytes": (ctypes.c_int64, [ctypes.c_void_p]),
+    "helm_profile_reset": (ctypes.c_int, [ctypes.c_void_p]),
+    "helm_profile_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(helm_profile)]),
     "helm_destroy": (None, [ctypes.c_void_p]),
     "helm_strerror": (ctypes.c_char_p, [ctypes.c_int]),
     "helm_last_error": (ctypes.c_char_p, []),
@@ -175,7 +190,7 @@ class Context:
 # ----------------------------------------------------------------------------- entry points
 def helm_setup(ndim, n, h, omega, m, pml_width, sigma0, nb, overlap, power=2,
                form=HELM_PML_LITERAL, cuts=None, sub_pml=0, precision=HELM_PREC_MIXED,
-               rhs_panel=0, restart=30, verbose=0, stream=None) -> Context:
+               rhs_panel=0, restart=30, verbose=0, stream=None, profile=0) -> Context:
     L = lib()
     nn = (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
     m = np.ascontiguousarray(m, dtype=np.float64)
@@ -193,7 +208,7 @@ def helm_setup(ndim, n, h, omega, m, pml_width, sigma0, nb, overlap, power=2,
     part.overlap = int(overlap)
     part.sub_pml = int(sub_pml)
     cfg = helm_config(int(precision), int(rhs_panel), int(restart), int(verbose),
-                      ctypes.c_void_p(stream) if stream else None)
+                      ctypes.c_void_p(stream) if stream else None, int(profile))
     out = ctypes.c_void_p()
     _check(L.helm_setup(ctypes.byref(out), int(ndim), nn, float(h), float(omega),
                         m.ctypes.data_as(ctypes.c_void_p), ctypes.byref(pml), ctypes.byref(part),
@@ -296,6 +311,16 @@ def helm_subdomain_solve(ctx: Context, s, R):
 
 def helm_device_bytes(ctx: Context) -> int:
     return int(lib().helm_device_bytes(ctx.ptr))
+
+
+def helm_profile_reset(ctx: Context):
+    _check(lib().helm_profile_reset(ctx.ptr), "helm_profile_reset")
+
+
+def helm_profile_get(ctx: Context) -> dict:
+    out = helm_profile()
+    _check(lib().helm_profile_get(ctx.ptr, ctypes.byref(out)), "helm_profile_get")
+    return out.as_dict()
 
 
 __all__ = [n for n in dir() if n.startswith("helm_") or n.startswith("HELM_")] + [

@@ -157,11 +157,67 @@ struct helm_ctx {
     double* scal_d = nullptr;
     size_t small_cap = 0;
     size_t dev_bytes = 0;
+
+    // profiling: per class counters and pending event pairs
+    helm_profile prof{};
+    struct Pending {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
 };
 
 namespace {
 
 size_t elem_size(const helm_ctx* c) { return c->prec == HELM_PREC_F64 ? 16 : 8; }
+
+cudaEvent_t pool_event(helm_ctx* c) {
+    if (!c->event_pool.empty()) {
+        cudaEvent_t e = c->event_pool.back();
+        c->event_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Bracket `launches` kernel launches of class cls with CUDA events on the
+// context's stream (when profiling) and count them.
+struct ProfScope {
+    helm_ctx* c;
+    int cls;
+    cudaEvent_t b = nullptr;
+    ProfScope(helm_ctx* c_, int cls_, int launches, double bytes = 0, double flops = 0)
+        : c(c_), cls(cls_) {
+        c->prof.launches[cls] += launches;
+        c->prof.bytes[cls] += bytes;
+        c->prof.flops[cls] += flops;
+        if (c->cfg.profile) {
+            b = pool_event(c);
+            cudaEventRecord(b, c->stream);
+        }
+    }
+    ~ProfScope() {
+        if (c->cfg.profile) {
+            cudaEvent_t e = pool_event(c);
+            cudaEventRecord(e, c->stream);
+            c->pending.push_back({cls, b, e});
+        }
+    }
+};
+
+// Resolve pending event pairs (the stream must be synchronised).
+void resolve_profile(helm_ctx* c) {
+    for (auto& p : c->pending) {
+        float ms = 0;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) c->prof.ms[p.cls] += ms;
+        c->event_pool.push_back(p.a);
+        c->event_pool.push_back(p.b);
+    }
+    c->pending.clear();
+}
 
 int ensure_buffers(helm_ctx* c, int nrhs) {
     if (nrhs <= c->cap_rhs && c->buf) return HELM_OK;
@@ -608,25 +664,43 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
     TRY(ensure_buffers(c, nrhs));
     const int64_t rs = c->buf_per_rhs;
     const int panel = auto_panel(c, nrhs);
+    const double es = (double)elem_size(c);
     for (size_t lv = 0; lv < c->levels.size(); ++lv) {
         const Task* t = c->tasks_d + c->level_off[lv];
         int nt = (int)c->levels[lv].size();
+        double gbytes = 0, sbytes = 0, sflops = 0;
+        for (const Task& tk : c->levels[lv]) {
+            const SubDesc& S = c->subs_h[tk.sub];
+            const double n = S.nblk, nl = S.nlines, passes = 2.0 * nl - 1.0;
+            gbytes += (double)S.win_elems * nrhs * es;
+            sbytes += passes * n * n * es + 4.0 * nl * n * nrhs * es;
+            sflops += passes * n * n * nrhs * 8.0;
+        }
         if (c->prec == HELM_PREC_F64) {
             auto* buf = static_cast<cplx<double>*>(c->buf);
-            launch_gather<double>(t, nt, c->max_win, c->subs_d, c->inc_d, c->P, c->m64, c->an64,
-                                  c->af64, c->tab64, b, nrhs, buf, rs, c->stream);
+            {
+                ProfScope ps(c, HELM_K_GATHER, 1, gbytes);
+                launch_gather<double>(t, nt, c->max_win, c->subs_d, c->inc_d, c->P, c->m64,
+                                      c->an64, c->af64, c->tab64, b, nrhs, buf, rs, c->stream);
+            }
+            ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
             launch_solve<double>(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
                                  static_cast<const double*>(c->fac), c->Pv64, c->inva64, buf, rs,
                                  c->stream);
         } else {
             auto* buf = static_cast<cplx<float>*>(c->buf);
-            launch_gather<float>(t, nt, c->max_win, c->subs_d, c->inc_d, c->P, c->m32, c->an32,
-                                 c->af32, c->tab32, b, nrhs, buf, rs, c->stream);
+            {
+                ProfScope ps(c, HELM_K_GATHER, 1, gbytes);
+                launch_gather<float>(t, nt, c->max_win, c->subs_d, c->inc_d, c->P, c->m32,
+                                     c->an32, c->af32, c->tab32, b, nrhs, buf, rs, c->stream);
+            }
+            ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
             launch_solve<float>(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
                                 static_cast<const float*>(c->fac), c->Pv32, c->inva32, buf, rs,
                                 c->stream);
         }
     }
+    ProfScope ps(c, HELM_K_ASSEMBLE, 1, (double)c->Ng * nrhs * 16.0);
     if (c->prec == HELM_PREC_F64)
         launch_assemble<double>(c->P, c->subs_d, c->box_of, c->node_buf_d, c->nsweeps, c->tab64,
                                 static_cast<const cplx<double>*>(c->buf), rs, nrhs, U, c->stream);
@@ -662,6 +736,7 @@ int stage_in(helm_ctx* c, const void* src, size_t bytes, int mem, Staged& out) {
 int stage_out(helm_ctx* c, void* dst, const Staged& s, size_t bytes, int mem) {
     if (mem == HELM_MEM_HOST) CK(cudaMemcpyAsync(dst, s.ptr, bytes, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
+    resolve_profile(c);
     return HELM_OK;
 }
 
@@ -699,7 +774,7 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
     std::vector<cplx<double>> hd((size_t)(m + 2) * nrhs);
     std::vector<double> sc(nrhs);
     auto norms = [&](const cplx<double>* v, std::vector<double>& out) -> int {
-        launch_dots(v, 0, 1, v, Ng, nrhs, c->small_d, c->partial_d, nblk, c->stream);
+        { ProfScope ps_(c, HELM_K_KRYLOV, 2); launch_dots(v, 0, 1, v, Ng, nrhs, c->small_d, c->partial_d, nblk, c->stream); }
         CK(cudaMemcpyAsync(hd.data(), c->small_d, nrhs * 16, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         for (int r = 0; r < nrhs; ++r) out[r] = std::sqrt(std::max(0.0, hd[r].re));
@@ -713,7 +788,7 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
     double maxres = 0;
     bool conv = false;
     while (true) {
-        launch_apply_A(c->P, c->gwin, c->m64, b, x, w, nrhs, c->stream);
+        { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_apply_A(c->P, c->gwin, c->m64, b, x, w, nrhs, c->stream); }
         std::vector<double> beta(nrhs);
         TRY(norms(w, beta));
         maxres = 0;
@@ -729,7 +804,7 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
         if (total >= maxit) break;
         for (int r = 0; r < nrhs; ++r) sc[r] = beta[r] > 0 ? 1.0 / beta[r] : 0.0;
         CK(cudaMemcpyAsync(c->scal_d, sc.data(), nrhs * 8, cudaMemcpyHostToDevice, c->stream));
-        launch_scale_vec(V(0), w, c->scal_d, Ng, nrhs, c->stream);
+        { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_scale_vec(V(0), w, c->scal_d, Ng, nrhs, c->stream); }
         // per-RHS Hessenberg (column-major, (m+1) x m), Givens, residual vector g
         std::vector<std::vector<cd>> H(nrhs, std::vector<cd>((size_t)(m + 1) * m, 0.0));
         std::vector<std::vector<double>> cs(nrhs, std::vector<double>(m, 0));
@@ -747,12 +822,12 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
             ++apps;
             // w = -A z_k (apply_A with no b); CGS2 on w: h = V^H w, w -= V h, twice.
             // Then A z_k = sum_i (-h_i) v_i + |w| v_{k+1} with v_{k+1} = -w/|w|.
-            launch_apply_A(c->P, c->gwin, c->m64, nullptr, Z(k), w, nrhs, c->stream);
+            { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_apply_A(c->P, c->gwin, c->m64, nullptr, Z(k), w, nrhs, c->stream); }
             std::vector<std::vector<cd>> hsum(nrhs, std::vector<cd>(k + 2, 0.0));
             for (int pass = 0; pass < 2; ++pass) {
                 for (int i = 0; i <= k; ++i)
-                    launch_dots(V(i), 0, 1, w, Ng, nrhs, c->small_d + (size_t)i * nrhs,
-                                c->partial_d, nblk, c->stream);
+                    { ProfScope ps_(c, HELM_K_KRYLOV, 2); launch_dots(V(i), 0, 1, w, Ng, nrhs, c->small_d + (size_t)i * nrhs,
+                                c->partial_d, nblk, c->stream); }
                 CK(cudaMemcpyAsync(hd.data(), c->small_d, (size_t)(k + 1) * nrhs * 16,
                                    cudaMemcpyDeviceToHost, c->stream));
                 CK(cudaStreamSynchronize(c->stream));
@@ -760,14 +835,14 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
                     for (int r = 0; r < nrhs; ++r)
                         hsum[r][i] += cd(hd[(size_t)i * nrhs + r].re, hd[(size_t)i * nrhs + r].im);
                 for (int i = 0; i <= k; ++i)
-                    launch_sub_combo(w, V(i), 0, 1, c->small_d + (size_t)i * nrhs, Ng, nrhs, -1.0,
-                                     c->stream);
+                    { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_sub_combo(w, V(i), 0, 1, c->small_d + (size_t)i * nrhs, Ng, nrhs, -1.0,
+                                     c->stream); }
             }
             std::vector<double> wn(nrhs);
             TRY(norms(w, wn));
             for (int r = 0; r < nrhs; ++r) sc[r] = wn[r] > 1e-300 ? -1.0 / wn[r] : 0.0;
             CK(cudaMemcpyAsync(c->scal_d, sc.data(), nrhs * 8, cudaMemcpyHostToDevice, c->stream));
-            launch_scale_vec(V(k + 1), w, c->scal_d, Ng, nrhs, c->stream);
+            { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_scale_vec(V(k + 1), w, c->scal_d, Ng, nrhs, c->stream); }
             ++total;
             bool all = true;
             maxres = 0;
@@ -823,7 +898,7 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
         CK(cudaMemcpyAsync(c->small_d, coef.data(), coef.size() * 16, cudaMemcpyHostToDevice,
                            c->stream));
         for (int i = 0; i < k; ++i)
-            launch_sub_combo(x, Z(i), 0, 1, c->small_d + (size_t)i * nrhs, Ng, nrhs, 1.0, c->stream);
+            { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_sub_combo(x, Z(i), 0, 1, c->small_d + (size_t)i * nrhs, Ng, nrhs, 1.0, c->stream); }
         CK(cudaStreamSynchronize(c->stream));
     }
     if (st) {
@@ -876,6 +951,12 @@ int helm_factor(helm_ctx* c) {
     }
     CK(cudaMemsetAsync(c->fac, 0, c->fac_bytes, c->stream));
     CK(cudaMemsetAsync(c->err_d, 0, sizeof(int), c->stream));
+    double fbytes = 0, fflops = 0;
+    for (const SubDesc& S : c->subs_h) {
+        fbytes += (double)S.nlines * S.nblk * S.nblk * elem_size(c);
+        fflops += (double)S.nlines * 8.0 * S.nblk * S.nblk * S.nblk;
+    }
+    ProfScope ps_(c, HELM_K_FACTOR, 1, fbytes, fflops);
     if (c->prec == HELM_PREC_F64)
         launch_factor_f64(c->subs_d, c->P.nsub, c->nbp_max, c->P, c->m64, c->an64, c->af64,
                           static_cast<double*>(c->fac), c->err_d, c->stream);
@@ -900,7 +981,7 @@ int helm_apply_ddm(helm_ctx* c, int nrhs, const void* F, void* U, int mem) {
     TRY(stage_in(c, F, bytes, mem, f));
     TRY(stage_in(c, mem == HELM_MEM_DEVICE ? U : nullptr, bytes, mem, u));
     TRY(ensure_bvec(c, nrhs));
-    launch_scale_J(c->P, c->gwin, f.ptr, c->bvec, nrhs, false, c->stream);
+    { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_scale_J(c->P, c->gwin, f.ptr, c->bvec, nrhs, false, c->stream); }
     TRY(apply_ddm_dev(c, nrhs, c->bvec, u.ptr));
     return stage_out(c, U, u, bytes, mem);
 }
@@ -919,9 +1000,9 @@ static int solve_common(helm_ctx* c, int nrhs, const void* F, void* U, int mem, 
     if (adjoint) {
         // A^H lam = g  <=>  A conj(lam) = conj(g)  (A^T = A)
         CK(cudaMemcpyAsync(c->bvec, f.ptr, bytes, cudaMemcpyDeviceToDevice, c->stream));
-        launch_conj(c->bvec, (int64_t)nrhs * c->Ng, c->stream);
+        { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_conj(c->bvec, (int64_t)nrhs * c->Ng, c->stream); }
     } else {
-        launch_scale_J(c->P, c->gwin, f.ptr, c->bvec, nrhs, false, c->stream);
+        { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_scale_J(c->P, c->gwin, f.ptr, c->bvec, nrhs, false, c->stream); }
     }
     int rc = gmres_dev(c, nrhs, c->bvec, u.ptr, rtol, maxit, st);
     if (rc != HELM_OK && rc != HELM_ERR_NO_CONVERGENCE) return rc;
@@ -958,7 +1039,7 @@ int helm_gradient(helm_ctx* c, int nsrc, const void* U, const void* L, double* g
         CK(cudaMalloc(&gd, c->Ng * 8));
         own = true;
     }
-    launch_gradient(c->P, c->gwin, u.ptr, l.ptr, nsrc, gd, c->stream);
+    { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_gradient(c->P, c->gwin, u.ptr, l.ptr, nsrc, gd, c->stream); }
     cudaError_t e = cudaGetLastError();
     if (e == cudaSuccess && own) e = cudaMemcpyAsync(grad, gd, c->Ng * 8, cudaMemcpyDeviceToHost, c->stream);
     if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
@@ -975,8 +1056,8 @@ int helm_residual(helm_ctx* c, int nrhs, const void* F, const void* U, void* R, 
     TRY(stage_in(c, U, bytes, mem, u));
     TRY(stage_in(c, mem == HELM_MEM_DEVICE ? R : nullptr, bytes, mem, r));
     TRY(ensure_bvec(c, nrhs));
-    launch_scale_J(c->P, c->gwin, f.ptr, c->bvec, nrhs, false, c->stream);
-    launch_apply_A(c->P, c->gwin, c->m64, c->bvec, u.ptr, r.ptr, nrhs, c->stream);
+    { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_scale_J(c->P, c->gwin, f.ptr, c->bvec, nrhs, false, c->stream); }
+    { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_apply_A(c->P, c->gwin, c->m64, c->bvec, u.ptr, r.ptr, nrhs, c->stream); }
     CK(cudaGetLastError());
     return stage_out(c, R, r, bytes, mem);
 }
@@ -1052,6 +1133,22 @@ int helm_problem_info(helm_ctx* c, int64_t* nsub, int64_t N[3]) {
 
 int64_t helm_device_bytes(helm_ctx* c) { return c ? (int64_t)c->dev_bytes : 0; }
 
+int helm_profile_reset(helm_ctx* c) {
+    if (!c) return fail(HELM_ERR_ARG, "null context");
+    CK(cudaStreamSynchronize(c->stream));
+    resolve_profile(c);
+    c->prof = helm_profile{};
+    return HELM_OK;
+}
+
+int helm_profile_get(helm_ctx* c, helm_profile* out) {
+    if (!c || !out) return fail(HELM_ERR_ARG, "bad argument");
+    CK(cudaStreamSynchronize(c->stream));
+    resolve_profile(c);
+    *out = c->prof;
+    return HELM_OK;
+}
+
 void helm_destroy(helm_ctx* c) {
     if (!c) return;
     void* ptrs[] = {c->subs_d, c->g_alpha, c->m64, c->m32, c->an64, c->af64, c->an32, c->af32,
@@ -1061,6 +1158,9 @@ void helm_destroy(helm_ctx* c) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto* p : c->gm) cudaFree(p);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    resolve_profile(c);
+    for (auto e : c->event_pool) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     delete c;
 }

@@ -152,10 +152,11 @@ void launch_factor_f64(const SubDesc* subs, int nsub, int nbp_max, const DevProb
                        const double* m64, const cplx<double>* an, const cplx<double>* af,
                        double* fac, int* err, cudaStream_t st);
 
+// err: device error word; set to 2 if a bounded wait for a bulk copy expired.
 template <typename T>
 void launch_solve(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                   int panel, const T* fac, const cplx<T>* Pv, const cplx<T>* inva, cplx<T>* buf,
-                  int64_t buf_rhs_stride, cudaStream_t st);
+                  int64_t buf_rhs_stride, int* err, cudaStream_t st);
 
 template <typename T>
 void launch_gather(const Task* tasks, int ntask, int64_t max_win, const SubDesc* subs,

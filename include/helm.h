@@ -166,6 +166,23 @@ int helm_residual(helm_ctx *ctx, int nrhs, const void *F, const void *U, void *R
  * overlap plus PML (helm_window_info).  For testing the factor and solve. */
 int helm_subdomain_solve(helm_ctx *ctx, int s, int nrhs, const void *R, void *U, int mem);
 
+/* The same subdomain solve as helm_subdomain_solve, for callers that cannot
+ * allocate device memory when they call it (code running inside an
+ * allocator callback, a loop with a fixed device-memory budget, or a host
+ * that has reserved all device memory up front).  The paper has no
+ * counterpart; this is a property of the library, not of the method.
+ * R and U are DEVICE pointers (complex128 [nrhs][window]) that the caller
+ * owns; nothing is allocated or freed.  The working buffer lives in one
+ * static device array of 64 MiB that every GPU loading the library holds
+ * until exit: nrhs times the window size times 8 bytes (complex64 context)
+ * or 16 bytes (complex128 context) must fit in 64 MiB - 256 bytes, else
+ * HELM_ERR_ARG with the sizes in helm_last_error().  The first call on a
+ * device looks up that array's device address (set-up work): make it before
+ * any stream capture.  Calls share the array and leave its contents behind;
+ * calls whose GPU work overlaps race on it.  Synchronises the context's
+ * stream before returning. */
+int helm_subdomain_solve_noalloc(helm_ctx *ctx, int s, int nrhs, const void *R, void *U);
+
 /* Window of subdomain s: lo[3], hi[3] full-grid node ranges (hi exclusive). */
 int helm_window_info(helm_ctx *ctx, int s, int64_t lo[3], int64_t hi[3]);
 

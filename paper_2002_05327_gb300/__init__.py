@@ -94,6 +94,8 @@ _SIGS = {
                                      ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
     "helm_subdomain_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
                                             ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int]),
+    "helm_subdomain_solve_noalloc": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_int,
+                                                    ctypes.c_void_p, ctypes.c_void_p]),
     "helm_window_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int,
                                         ctypes.POINTER(ctypes.c_int64),
                                         ctypes.POINTER(ctypes.c_int64)]),
@@ -306,6 +308,20 @@ def helm_subdomain_solve(ctx: Context, s, R):
     up, _, ku = _ptr_mem(U, np.complex128)
     _check(lib().helm_subdomain_solve(ctx.ptr, int(s), R.shape[0], rp, up, mem),
            "helm_subdomain_solve")
+    return U
+
+
+def helm_subdomain_solve_noalloc(ctx: Context, s, R):
+    """Subdomain solve that allocates no device memory (see include/helm.h):
+    R is a CUDA complex128 tensor [nrhs, *window]; returns U of the same shape
+    (the output tensor is allocated here, by torch, before the call)."""
+    if not _is_torch(R):
+        raise TypeError("helm_subdomain_solve_noalloc takes CUDA tensors")
+    rp, _, kr = _ptr_mem(R, np.complex128)
+    U = _empty_like(R, tuple(R.shape), np.complex128)
+    up, _, ku = _ptr_mem(U, np.complex128)
+    _check(lib().helm_subdomain_solve_noalloc(ctx.ptr, int(s), R.shape[0], rp, up),
+           "helm_subdomain_solve_noalloc")
     return U
 
 

@@ -1132,6 +1132,37 @@ int helm_subdomain_solve(helm_ctx* c, int s, int nrhs, const void* R, void* U, i
     return HELM_OK;
 }
 
+int helm_subdomain_solve_noalloc(helm_ctx* c, int s, int nrhs, const void* R, void* U) {
+    if (!c || !R || !U || nrhs < 1 || s < 0 || s >= c->P.nsub)
+        return fail(HELM_ERR_ARG, "bad argument");
+    if (!c->factored) return fail(HELM_ERR_NOT_FACTORED, "call helm_factor first");
+    const SubDesc& S = c->subs_h[s];
+    const size_t need = (size_t)nrhs * S.win_elems * elem_size(c);
+    if (need > noalloc_capacity_bytes())
+        return fail(HELM_ERR_ARG, "helm_subdomain_solve_noalloc: " + std::to_string(nrhs) +
+                                      " right-hand sides on this window need " +
+                                      std::to_string(need) + " bytes of scratch; the maximum is " +
+                                      std::to_string(noalloc_capacity_bytes()));
+    NoAllocArgs a;
+    a.f64 = c->prec == HELM_PREC_F64;
+    a.sub = s;
+    a.nrhs = nrhs;
+    a.nbp_max = c->nbp_max;
+    a.panel = auto_panel(c, nrhs);
+    a.win_elems = S.win_elems;
+    a.subs = c->subs_d;
+    a.fac = c->fac;
+    a.Pv = a.f64 ? (const void*)c->Pv64 : (const void*)c->Pv32;
+    a.inva = a.f64 ? (const void*)c->inva64 : (const void*)c->inva32;
+    a.R = static_cast<const cplx<double>*>(R);
+    a.U = static_cast<cplx<double>*>(U);
+    a.err = c->err_d;
+    a.stream = c->stream;
+    CK(noalloc_subdomain_solve(a));
+    CK(cudaStreamSynchronize(c->stream));
+    return check_device_error(c);
+}
+
 int helm_window_info(helm_ctx* c, int s, int64_t lo[3], int64_t hi[3]) {
     if (!c || s < 0 || s >= c->P.nsub || !lo || !hi) return fail(HELM_ERR_ARG, "bad argument");
     for (int a = 0; a < 3; ++a) {

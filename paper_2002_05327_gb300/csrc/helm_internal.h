@@ -188,4 +188,21 @@ void launch_conj(cplx<double>* v, int64_t count, cudaStream_t st);
 void launch_gradient(const DevProblem& P, const Win<double>& g, const cplx<double>* U,
                      const cplx<double>* L, int nsrc, double* grad, cudaStream_t st);
 
+// Subdomain solve inside a static device scratch array (k_noalloc.cu).
+struct NoAllocArgs {
+    bool f64;
+    int sub, nrhs, nbp_max, panel;
+    int64_t win_elems;
+    const SubDesc* subs;
+    const void* fac;
+    const void* Pv;
+    const void* inva;
+    const cplx<double>* R;
+    cplx<double>* U;
+    int* err;
+    cudaStream_t stream;
+};
+size_t noalloc_capacity_bytes();
+cudaError_t noalloc_subdomain_solve(const NoAllocArgs& a);
+
 }  // namespace helm

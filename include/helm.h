@@ -56,7 +56,9 @@ enum helm_status {
 
 enum helm_precision {
     HELM_PREC_F64 = 0,   /* complex128 factors and local solves (plain FP64 DDM) */
-    HELM_PREC_MIXED = 1  /* complex64 factors and local solves, FP64 outer GMRES */
+    HELM_PREC_MIXED = 1, /* complex64 factors and local solves, FP64 outer GMRES */
+    HELM_PREC_TF32 = 2   /* complex64 factors, local block products on the tensor
+                            cores in TF32 with FP32 accumulation, FP64 outer GMRES */
 };
 
 enum helm_pml_form {

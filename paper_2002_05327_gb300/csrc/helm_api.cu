@@ -346,7 +346,9 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
         return fail(HELM_ERR_ARG, "invalid PML");
     if (part->overlap < 1) return fail(HELM_ERR_ARG, "overlap must be >= 1");
     if (cfg) c->cfg = *cfg;
-    c->prec = (cfg && cfg->precision == HELM_PREC_F64) ? HELM_PREC_F64 : HELM_PREC_MIXED;
+    c->prec = HELM_PREC_MIXED;
+    if (cfg && (cfg->precision == HELM_PREC_F64 || cfg->precision == HELM_PREC_TF32))
+        c->prec = cfg->precision;
     if (c->cfg.restart <= 0) c->cfg.restart = 30;
     c->pml = *pml;
     c->W = part->sub_pml > 0 ? part->sub_pml : pml->width;
@@ -493,8 +495,13 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
         S.nblk = 1;
         for (int a = 0; a < slow; ++a) S.nblk *= S.nw[a];
         S.nlines = S.nw[slow];
-        S.nbp = (S.nblk + 31) / 32 * 32;
-        if (S.nbp > 1024) return fail(HELM_ERR_ARG, "subdomain block larger than 1024 nodes");
+        // padded block size with nbp = 8 (mod 32): the four column planes an
+        // m16n8k8 A fragment touches then fall in disjoint shared-memory banks
+        {
+            const int m16 = (S.nblk + 15) / 16 * 16;
+            S.nbp = m16 + ((8 - m16 % 32) + 32) % 32;
+        }
+        if (S.nbp > 1280) return fail(HELM_ERR_ARG, "subdomain block larger than 1280 nodes");
         S.win_elems = (int64_t)S.nw[0] * S.nw[1] * S.nw[2];
         S.fac_off = fac_elems;
         fac_elems += (int64_t)S.nlines * 2 * S.nbp * S.nbp;
@@ -651,7 +658,8 @@ int auto_panel(const helm_ctx* c, int nrhs) {
         p = nrhs >= 16 ? 4 : nrhs >= 2 ? 2 : 1;
     }
     // register budget of solve_kernel: 8 complex64 or 4 complex128 columns per thread
-    const int pmax = c->prec == HELM_PREC_F64 ? 4 : 8;
+    int pmax = c->prec == HELM_PREC_F64 ? 4 : 8;
+    if (c->nbp_max > 960) pmax = 2;  // two rows per thread (plane blocks)
     if (p > pmax) p = pmax;
     int q = 1;
     while (q < p) q <<= 1;
@@ -696,9 +704,14 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
                                      c->an32, c->af32, c->tab32, b, nrhs, buf, rs, c->stream);
             }
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
-            launch_solve<float>(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
+            if (c->prec == HELM_PREC_TF32)
+                launch_solve_tc(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
                                 static_cast<const float*>(c->fac), c->Pv32, c->inva32, buf, rs,
                                 c->err_d, c->stream);
+            else
+                launch_solve<float>(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
+                                    static_cast<const float*>(c->fac), c->Pv32, c->inva32, buf,
+                                    rs, c->err_d, c->stream);
         }
     }
     ProfScope ps(c, HELM_K_ASSEMBLE, 1, (double)c->Ng * nrhs * 16.0);
@@ -980,6 +993,9 @@ int helm_factor(helm_ctx* c) {
     else
         launch_factor_f32(c->subs_d, c->P.nsub, c->nbp_max, c->P, c->m32, c->an32, c->af32,
                           static_cast<float*>(c->fac), c->err_d, c->stream);
+    if (c->prec == HELM_PREC_TF32)
+        launch_round_tf32(static_cast<float*>(c->fac), (int64_t)(c->fac_bytes / sizeof(float)),
+                          c->stream);
     CK(cudaGetLastError());
     int err = 0;
     CK(cudaMemcpyAsync(&err, c->err_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -1109,6 +1125,10 @@ int helm_subdomain_solve(helm_ctx* c, int s, int nrhs, const void* R, void* U, i
         launch_solve<double>(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
                              static_cast<const double*>(c->fac), c->Pv64, c->inva64,
                              static_cast<cplx<double>*>(wb), we, c->err_d, c->stream);
+    else if (c->prec == HELM_PREC_TF32)
+        launch_solve_tc(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
+                        static_cast<const float*>(c->fac), c->Pv32, c->inva32,
+                        static_cast<cplx<float>*>(wb), we, c->err_d, c->stream);
     else
         launch_solve<float>(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
                             static_cast<const float*>(c->fac), c->Pv32, c->inva32,

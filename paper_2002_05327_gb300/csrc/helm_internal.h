@@ -158,6 +158,12 @@ void launch_solve(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max
                   int panel, const T* fac, const cplx<T>* Pv, const cplx<T>* inva, cplx<T>* buf,
                   int64_t buf_rhs_stride, int* err, cudaStream_t st);
 
+// Tensor-core (TF32 mma, FP32 accumulate) variant for complex64 factors.
+void launch_solve_tc(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
+                     int panel, const float* fac, const cplx<float>* Pv, const cplx<float>* inva,
+                     cplx<float>* buf, int64_t buf_rhs_stride, int* err, cudaStream_t st);
+void launch_round_tf32(float* x, int64_t count, cudaStream_t st);
+
 template <typename T>
 void launch_gather(const Task* tasks, int ntask, int64_t max_win, const SubDesc* subs,
                    const Incoming* inc, const DevProblem& P, const T* m, const cplx<T>* an,

@@ -7,19 +7,27 @@
 // with a_j[p] = Pv[p] / alpha_slow(face j), c_j[p] = Pv[p] / alpha_slow(face j+1),
 // Pv[p] = prod of the non-slow alphas at block node p over h^2.
 //
-// Work split: one CTA per (task, panel of PG right-hand sides); thread p owns
-// row p of the block for all PG columns.  The right-hand side panel (n x PG)
-// sits in shared memory as [q][c].  D_j is stored column-major with split
-// planes (column q = nbp reals then nbp imaginaries), so CQ whole columns are
-// one contiguous span: thread 0 streams D through a ring of NSTAGE shared
-// buffers with cp.async.bulk (the bulk-copy engine) and mbarrier completion,
-// running NSTAGE chunks ahead -- across line boundaries and from the forward
-// into the backward pass, since D does not depend on the recurrence.  Every
-// mbarrier wait is bounded; on expiry the CTA raises the error word, drains
-// its copies in flight (bounded) and leaves.
+// One CTA per (task, panel of PG right-hand sides).  Consumer threads own
+// RPT rows of the block each, for all PG columns; one producer warp streams D.
+// D_j is stored column-major with split planes (column q = nbp reals then nbp
+// imaginaries), so cq whole columns form one contiguous span: the producer
+// copies them with cp.async.bulk into a ring of NS shared stages (full
+// barrier: bytes landed; empty barrier: every consumer warp is done with the
+// stage), running ahead across line boundaries and from the forward into the
+// backward pass (D does not depend on the recurrence).  The right-hand side
+// panel of line j (n x PG, [q][c]) is double-buffered, so each line needs a
+// single barrier among the consumers.  The global operands of the next step
+// (b_{j+1} forward, y_j backward) are loaded before the block product so
+// their latency hides behind it.
+//
+// Every mbarrier wait is bounded.  On expiry the CTA raises the device error
+// word, stops issuing copies, finishes the line without further waits,
+// drains the copies still in flight (bounded) and leaves.
 //
 // The window buffer holds b on entry, y after the forward pass and u on exit
 // (layout [rhs][line][p]).
+#include <algorithm>
+
 #include "helm_internal.h"
 
 namespace helm {
@@ -35,6 +43,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                  "r"(bytes)
                  : "memory");
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -42,7 +53,7 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
         "l"(src), "r"(bytes), "r"(smem_u32(bar))
         : "memory");
 }
-// Bounded wait on an mbarrier phase; returns false if the limit expired.
+// Bounded wait for the completion of the phase with the given parity.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32_t limit) {
     uint32_t done = 0;
     for (uint32_t it = 0; it < limit; ++it) {
@@ -57,12 +68,27 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, uint32
     }
     return false;
 }
+// Barrier among the consumer threads that also ORs a flag across them, so
+// every consumer takes the same abort decision.
+__device__ __forceinline__ bool consumers_sync_any(int nthreads, int flag) {
+    uint32_t out;
+    asm volatile(
+        "{\n\t.reg .pred q, p;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, 1, %2, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(out)
+        : "r"(flag), "r"(nthreads)
+        : "memory");
+    return out != 0;
+}
 
-constexpr uint32_t kWaitLimit = 1u << 22;  // try_wait rounds (each suspends up to a time slice)
+constexpr uint32_t kWaitLimit = 1u << 22;
 
 struct SolveGeom {
-    int cq;      // columns per chunk
-    int nstage;  // ring depth
+    int cq;       // columns per chunk
+    int nstage;   // ring depth
+    int ncons;    // consumer threads (multiple of 32)
 };
 
 // Chunk sequence: forward lines 0..L-1 then backward lines L-2..0, each line
@@ -80,7 +106,7 @@ struct ChunkSeq {
     __device__ __forceinline__ int col0(int i) const { return (i % per_line) * cq; }
 };
 
-template <typename T, int PG>
+template <typename T, int PG, int RPT>
 __global__ void __launch_bounds__(1024) solve_kernel(const Task* __restrict__ tasks,
                                                      const SubDesc* __restrict__ subs, int nrhs,
                                                      const T* __restrict__ fac,
@@ -92,156 +118,210 @@ __global__ void __launch_bounds__(1024) solve_kernel(const Task* __restrict__ ta
     const Task tk = tasks[blockIdx.x];
     const SubDesc& S = subs[tk.sub];
     const int n = S.nblk, nbp = S.nbp, nl = S.nlines;
-    const int cq = G.cq, NS = G.nstage;
+    const int cq = G.cq, NS = G.nstage, NC = G.ncons;
     const size_t stage_elems = (size_t)cq * 2 * nbp_max;
     T* stages = reinterpret_cast<T*>(smem_raw);
-    cplx<T>* rs = reinterpret_cast<cplx<T>*>(stages + stage_elems * NS);  // [nbp_max][PG]
-    uint64_t* full = reinterpret_cast<uint64_t*>(rs + (size_t)nbp_max * PG);
-    __shared__ int abort_flag;
-
-    const int c0 = blockIdx.y * PG;
-    const int p = threadIdx.x;
-    const bool row = p < n;
-    const cplx<T>* pv = Pv + S.coup_off;
-    const cplx<T>* ia = inva + S.inva_off;
-    const cplx<T> pvp = row ? pv[p] : mk<T>(0, 0);
-    cplx<T>* V = buf + tk.buf_off;
-    int ncol = nrhs - c0;
-    if (ncol > PG) ncol = PG;
+    cplx<T>* rs = reinterpret_cast<cplx<T>*>(stages + stage_elems * NS);  // [2][nbp_max][PG]
+    uint64_t* full = reinterpret_cast<uint64_t*>(rs + (size_t)2 * nbp_max * PG);
+    uint64_t* empty = full + NS;
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(empty + NS);
 
     const ChunkSeq seq(n, nl, cq);
-    const T* fbase = fac + S.fac_off;
-    const size_t line_elems = (size_t)2 * nbp * nbp;
-    auto issue = [&](int i) {  // thread 0 only
-        const int s = i % NS;
-        const int l = seq.line_of(i), q0 = seq.col0(i);
-        const int cols = min(cq, n - q0);
-        const uint32_t bytes = (uint32_t)(cols * 2 * nbp * sizeof(T));
-        mbar_expect_tx(&full[s], bytes);
-        bulk_g2s(stages + s * stage_elems, fbase + l * line_elems + (size_t)q0 * 2 * nbp, bytes,
-                 &full[s]);
-    };
-    if (p == 0) {
-        abort_flag = 0;
-        for (int s = 0; s < NS; ++s) mbar_init(&full[s], 1);
+    const int tid = threadIdx.x;
+    const int ncw = NC / 32;
+    if (tid == 0) {
+        *abort_flag = 0;
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], ncw);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (p == 0)
-        for (int i = 0; i < NS && i < seq.total; ++i) issue(i);
 
-    cplx<T> prev[PG], acc[PG];
-#pragma unroll
-    for (int c = 0; c < PG; ++c) prev[c] = mk<T>(0, 0);
+    // ======================================================= producer warp
+    if (tid >= NC) {
+        if (tid != NC) return;
+        const T* fbase = fac + S.fac_off;
+        const size_t line_elems = (size_t)2 * nbp * nbp;
+        int issued = 0;
+        for (int i = 0; i < seq.total; ++i) {
+            const int s = i % NS;
+            if (i >= NS && !mbar_wait(&empty[s], (uint32_t)(((i / NS) - 1) & 1), kWaitLimit)) {
+                atomicExch(err, 2);
+                *abort_flag = 1;
+            }
+            if (*abort_flag) break;
+            const int l = seq.line_of(i), q0 = seq.col0(i);
+            const int cols = min(cq, n - q0);
+            const uint32_t bytes = (uint32_t)(cols * 2 * nbp * sizeof(T));
+            mbar_expect_tx(&full[s], bytes);
+            bulk_g2s(stages + s * stage_elems, fbase + l * line_elems + (size_t)q0 * 2 * nbp, bytes,
+                     &full[s]);
+            issued = i + 1;
+        }
+        // drain: every issued copy must land before the CTA's shared memory is released
+        for (int i = max(0, issued - NS); i < issued; ++i)
+            mbar_wait(&full[i % NS], (uint32_t)((i / NS) & 1), kWaitLimit);
+        return;
+    }
 
-    int ci = 0;  // next chunk to consume
-    bool ok = true;
-    // multiply the staged panel rs by D_j, chunk by chunk, into acc
-    auto line_gemv = [&]() {
+    // ======================================================= consumers
+    const int c0 = blockIdx.y * PG;
+    int ncol = nrhs - c0;
+    if (ncol > PG) ncol = PG;
+    const cplx<T>* pv = Pv + S.coup_off;
+    const cplx<T>* ia = inva + S.inva_off;
+    cplx<T>* V = buf + tk.buf_off;
+    int prow[RPT];
+    bool row[RPT];
+    cplx<T> pvp[RPT];
 #pragma unroll
-        for (int c = 0; c < PG; ++c) acc[c] = mk<T>(0, 0);
+    for (int r = 0; r < RPT; ++r) {
+        prow[r] = tid + r * NC;
+        row[r] = prow[r] < n;
+        pvp[r] = row[r] ? pv[prow[r]] : mk<T>(0, 0);
+    }
+    auto vidx = [&](int c, int j, int pp) -> int64_t {
+        return (int64_t)(c0 + c) * rstride + (int64_t)j * n + pp;
+    };
+
+    cplx<T> prev[RPT][PG], acc[RPT][PG], pre[RPT][PG];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r)
+#pragma unroll
+        for (int c = 0; c < PG; ++c) {
+            prev[r][c] = mk<T>(0, 0);
+            pre[r][c] = (row[r] && c < ncol) ? V[vidx(c, 0, prow[r])] : mk<T>(0, 0);
+        }
+
+    int ci = 0;
+    int rb = 0;  // panel buffer of the current line
+    auto line_gemv = [&](const cplx<T>* panel) {
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+            for (int c = 0; c < PG; ++c) acc[r][c] = mk<T>(0, 0);
         for (int k = 0; k < seq.per_line; ++k, ++ci) {
             const int s = ci % NS;
-            const uint32_t parity = (uint32_t)((ci / NS) & 1);
-            if (!mbar_wait(&full[s], parity, kWaitLimit)) {
+            if (!*abort_flag && !mbar_wait(&full[s], (uint32_t)((ci / NS) & 1), kWaitLimit)) {
                 atomicExch(err, 2);
-                abort_flag = 1;
-            }
-            __syncthreads();
-            if (abort_flag) {
-                ok = false;
-                return;
+                *abort_flag = 1;
             }
             const int q0 = seq.col0(ci);
             const int cols = min(cq, n - q0);
-            if (row) {
-                const T* Dc = stages + s * stage_elems + p;
+            const T* st = stages + s * stage_elems;
 #pragma unroll 4
-                for (int qq = 0; qq < cols; ++qq) {
-                    const cplx<T> d = mk<T>(Dc[(size_t)qq * 2 * nbp], Dc[(size_t)qq * 2 * nbp + nbp]);
-                    const cplx<T>* r = rs + (size_t)(q0 + qq) * PG;
+            for (int qq = 0; qq < cols; ++qq) {
+                const cplx<T>* rq = panel + (size_t)(q0 + qq) * PG;
+                cplx<T> rv[PG];
 #pragma unroll
-                    for (int c = 0; c < PG; ++c) cfma(acc[c], d, r[c]);
+                for (int c = 0; c < PG; ++c) rv[c] = rq[c];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    const T* Dc = st + (size_t)qq * 2 * nbp + prow[r];
+                    const cplx<T> d = row[r] ? mk<T>(Dc[0], Dc[nbp]) : mk<T>(0, 0);
+#pragma unroll
+                    for (int c = 0; c < PG; ++c) cfma(acc[r][c], d, rv[c]);
                 }
             }
-            __syncthreads();
-            if (p == 0 && ci + NS < seq.total) issue(ci + NS);
+            __syncwarp();
+            if ((tid & 31) == 0) mbar_arrive(&empty[s]);
         }
     };
 
-    // ---------------- forward
-    for (int j = 0; j < nl && ok; ++j) {
-        if (row) {
-            cplx<T> a = (j > 0) ? pvp * ia[j] : mk<T>(0, 0);
+    // ---------------- forward: pre holds b_j on entry to line j
+    for (int j = 0; j < nl; ++j) {
+        cplx<T>* panel = rs + (size_t)rb * nbp_max * PG;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            if (!row[r]) continue;
+            cplx<T> a = (j > 0) ? pvp[r] * ia[j] : mk<T>(0, 0);
+#pragma unroll
+            for (int c = 0; c < PG; ++c) panel[prow[r] * PG + c] = pre[r][c] - a * prev[r][c];
+        }
+        if (consumers_sync_any(NC, *abort_flag)) return;
+        // prefetch b_{j+1}
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+            for (int c = 0; c < PG; ++c)
+                pre[r][c] = (row[r] && c < ncol && j + 1 < nl) ? V[vidx(c, j + 1, prow[r])]
+                                                                : mk<T>(0, 0);
+        line_gemv(panel);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
 #pragma unroll
             for (int c = 0; c < PG; ++c) {
-                cplx<T> v = mk<T>(0, 0);
-                if (c < ncol) v = V[(int64_t)(c0 + c) * rstride + (int64_t)j * n + p] - a * prev[c];
-                rs[p * PG + c] = v;
+                prev[r][c] = acc[r][c];
+                if (row[r] && c < ncol) V[vidx(c, j, prow[r])] = acc[r][c];
             }
-        }
-        __syncthreads();
-        line_gemv();
-        if (!ok) break;
-        if (row) {
-#pragma unroll
-            for (int c = 0; c < PG; ++c) {
-                prev[c] = acc[c];
-                if (c < ncol) V[(int64_t)(c0 + c) * rstride + (int64_t)j * n + p] = acc[c];
-            }
-        }
+        rb ^= 1;
     }
-    // ---------------- backward (prev = u_{L-1} = y_{L-1})
-    for (int j = nl - 2; j >= 0 && ok; --j) {
-        if (row) {
-            cplx<T> cc = pvp * ia[j + 1];
+    // ---------------- backward: prev = u_{j+1}
+    for (int j = nl - 2; j >= 0; --j) {
+        cplx<T>* panel = rs + (size_t)rb * nbp_max * PG;
 #pragma unroll
-            for (int c = 0; c < PG; ++c) rs[p * PG + c] = cc * prev[c];
+        for (int r = 0; r < RPT; ++r) {
+            if (!row[r]) continue;
+            cplx<T> cc = pvp[r] * ia[j + 1];
+#pragma unroll
+            for (int c = 0; c < PG; ++c) panel[prow[r] * PG + c] = cc * prev[r][c];
         }
-        __syncthreads();
-        line_gemv();
-        if (!ok) break;
-        if (row) {
+        if (consumers_sync_any(NC, *abort_flag)) return;
+        // y_j, needed after the product
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
+#pragma unroll
+            for (int c = 0; c < PG; ++c)
+                pre[r][c] = (row[r] && c < ncol) ? V[vidx(c, j, prow[r])] : mk<T>(0, 0);
+        line_gemv(panel);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r)
 #pragma unroll
             for (int c = 0; c < PG; ++c) {
-                cplx<T> y = (c < ncol) ? V[(int64_t)(c0 + c) * rstride + (int64_t)j * n + p]
-                                       : mk<T>(0, 0);
-                prev[c] = y - acc[c];
-                if (c < ncol) V[(int64_t)(c0 + c) * rstride + (int64_t)j * n + p] = prev[c];
+                prev[r][c] = pre[r][c] - acc[r][c];
+                if (row[r] && c < ncol) V[vidx(c, j, prow[r])] = prev[r][c];
             }
-        }
-    }
-    if (!ok && p == 0) {
-        // drain: wait (bounded) for every copy still in flight before leaving
-        for (int i = ci; i < seq.total && i < ci + NS; ++i)
-            mbar_wait(&full[i % NS], (uint32_t)((i / NS) & 1), kWaitLimit);
+        rb ^= 1;
     }
 }
 
-static SolveGeom geom_for(int nbp_max, size_t esize, int PG, size_t* smem) {
+static SolveGeom geom_for(int nbp_max, size_t esize, int PG, int RPT, size_t* smem) {
     SolveGeom g;
+    g.ncons = ((nbp_max + RPT - 1) / RPT + 31) / 32 * 32;
     const size_t col_bytes = 2 * (size_t)nbp_max * esize;
-    g.cq = (int)std::max<size_t>(1, (48 * 1024) / col_bytes);
-    const size_t rs_bytes = (size_t)nbp_max * PG * 2 * esize;
+    g.cq = (int)std::max<size_t>(1, (32 * 1024) / col_bytes);
+    const size_t rs_bytes = (size_t)2 * nbp_max * PG * 2 * esize;
     const size_t budget = 200 * 1024;
-    g.nstage = 4;
-    while (g.nstage > 2 && g.nstage * g.cq * col_bytes + rs_bytes + 64 > budget) --g.nstage;
-    while (g.nstage * g.cq * col_bytes + rs_bytes + 64 > budget && g.cq > 1) --g.cq;
-    *smem = g.nstage * g.cq * col_bytes + rs_bytes + 8 * g.nstage + 16;
+    g.nstage = 6;
+    while (g.nstage > 2 && g.nstage * g.cq * col_bytes + rs_bytes + 256 > budget) --g.nstage;
+    while (g.nstage * g.cq * col_bytes + rs_bytes + 256 > budget && g.cq > 1) --g.cq;
+    *smem = g.nstage * g.cq * col_bytes + rs_bytes + 16 * g.nstage + 16;
     return g;
+}
+
+template <typename T, int PG, int RPT>
+static void launch_cfg(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
+                       const T* fac, const cplx<T>* Pv, const cplx<T>* inva, cplx<T>* buf,
+                       int64_t rstride, int* err, cudaStream_t st) {
+    size_t smem = 0;
+    SolveGeom g = geom_for(nbp_max, sizeof(T), PG, RPT, &smem);
+    cudaFuncSetAttribute(solve_kernel<T, PG, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)smem);
+    dim3 grid(ntask, (nrhs + PG - 1) / PG);
+    solve_kernel<T, PG, RPT><<<grid, g.ncons + 32, smem, st>>>(tasks, subs, nrhs, fac, Pv, inva,
+                                                               buf, rstride, g, nbp_max, err);
 }
 
 template <typename T, int PG>
 static void launch_pg(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                       const T* fac, const cplx<T>* Pv, const cplx<T>* inva, cplx<T>* buf,
                       int64_t rstride, int* err, cudaStream_t st) {
-    size_t smem = 0;
-    SolveGeom g = geom_for(nbp_max, sizeof(T), PG, &smem);
-    cudaFuncSetAttribute(solve_kernel<T, PG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)smem);
-    dim3 grid(ntask, (nrhs + PG - 1) / PG);
-    solve_kernel<T, PG><<<grid, nbp_max, smem, st>>>(tasks, subs, nrhs, fac, Pv, inva, buf,
-                                                      rstride, g, nbp_max, err);
+    if (nbp_max <= 960)
+        launch_cfg<T, PG, 1>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, err, st);
+    else
+        launch_cfg<T, PG, 2>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, err, st);
 }
 
 template <typename T>

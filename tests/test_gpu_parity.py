@@ -8,6 +8,9 @@ Tolerances (relative L2 over the whole output):
     unit roundoff of 6e-8; the block recurrence over ~50-200 lines and the
     explicit inverses amplify it by the local condition numbers (~1e2-1e3 on
     these PML blocks).
+  * Tensor-core path (HELM_PREC_TF32), raw DDM: 3e-2.  TF32 keeps 10
+    mantissa bits (unit roundoff 4.9e-4) in every block product; the same
+    amplification as above applies.
   * After FP64 GMRES (the product's answer): 1e-6 against the global direct
     solve, the bound the method promises after refinement.
 """
@@ -23,7 +26,7 @@ from oracle import helmholtz as OH
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-10, 1: 1e-3}
+TOL = {0: 1e-10, 1: 1e-3, 2: 3e-2}
 
 
 @pytest.fixture(scope="module")
@@ -66,7 +69,7 @@ def _nonuniform():
 CASES["2d-nonuniform-3x3"] = _nonuniform
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_apply_ddm_matches_algorithm(H, case, prec):
     """helm_apply_ddm equals the oracle's Algorithm 3.1 / 4.1 (same windows,
@@ -79,7 +82,7 @@ def test_apply_ddm_matches_algorithm(H, case, prec):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_subdomain_solve_matches_local_direct_solve(H, prec):
     wl = W.small_2d(nx=60, ny=52, nbx=4, nby=3, nrhs=3)
     ctx = _ctx(H, wl, prec)
@@ -93,7 +96,7 @@ def test_subdomain_solve_matches_local_direct_solve(H, prec):
         R = rng.standard_normal((3,) + sub.shape) + 1j * rng.standard_normal((3,) + sub.shape)
         u = H.helm_subdomain_solve(ctx, s, R)
         ref = part.local_solve(sub, R)
-        assert rel(u, ref) < (1e-11 if prec == 0 else 1e-4), (s, rel(u, ref))
+        assert rel(u, ref) < {0: 1e-11, 1: 1e-4, 2: 1e-2}[prec], (s, rel(u, ref))
     ctx.close()
 
 
@@ -110,7 +113,7 @@ def test_config1_ddm_fp64(H):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 2])
 def test_gmres_reaches_global_solution(H, prec):
     wl = W.small_2d(nx=64, ny=56, nbx=3, nby=3, pml=10, overlap=4, sub_pml=10, nrhs=3)
     ctx = _ctx(H, wl, prec)

@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", type=int, default=2, help="workload number (2 = bench)")
+    ap.add_argument("--prec", default="tf32", choices=["tf32", "mixed"],
+                    help="precision of the subdomain factors/solves of the product path")
     ap.add_argument("--nrhs", type=int, default=0,
                     help="use only the first NRHS sources (profiling runs); 0 = all")
     return ap.parse_args()
@@ -219,7 +221,8 @@ def main():
 
     # ---------------- mixed precision (the product path)
     stream = torch.cuda.current_stream(dev).cuda_stream
-    ctx = H.helm_setup_workload(wl, precision=H.HELM_PREC_MIXED, profile=1, stream=stream)
+    prec = H.HELM_PREC_TF32 if args.prec == "tf32" else H.HELM_PREC_MIXED
+    ctx = H.helm_setup_workload(wl, precision=prec, profile=1, stream=stream)
     t0 = time.time()
     H.helm_factor(ctx)
     factor_ms = (time.time() - t0) * 1e3
@@ -317,17 +320,22 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "vs_baseline": None, "dtype": "tf32" if args.prec == "tf32" else "c64",
+        "data": "synthetic",
         "config": {"workload": wl.name, "grid": list(wl.N), "h_m": wl.h, "freq_hz": 15,
                    "nb": list(wl.nb), "overlap": wl.overlap, "sub_pml": wl.sub_pml,
                    "nrhs": nrhs, "rtol": args.rtol, "outer": "FP64 flexible GMRES",
+                   "subdomain_precision": ("complex64 factors, TF32 tensor-core block products, "
+                                           "FP32 accumulation") if args.prec == "tf32"
+                   else "complex64 factors and FP32 block products",
                    "l2": "inputs larger than L2 (device working set %.1f GB, RHS %.2f GB)" % (
                        dev_bytes / 1e9, nrhs * np.prod(wl.N) * 16 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "gmres": {"iters": iters, "applications": apps, "max_rel_resid": res,
                   "factor_ms": factor_ms, "levels": stats[0]["levels"],
                   "subdomain_solves_per_application": stats[0]["solves"]},
-        "roofline": {"kernel": "solve_kernel (subdomain forward/backward block solves)",
+        "roofline": {"kernel": ("solve_tc_kernel" if args.prec == "tf32" else "solve_kernel")
+                     + " (subdomain forward/backward block solves)",
                      "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm, "traffic": None, "peak_source": peak_src,
                      "tflops_achieved": tflops,

@@ -102,6 +102,8 @@ typedef struct {
     int32_t verbose;    /* 1: per-iteration residuals on stderr */
     void *stream;       /* cudaStream_t to run on; NULL = the library's own stream */
     int32_t profile;    /* 1: time every kernel launch with CUDA events (helm_profile_get) */
+    int32_t tc_kernel;  /* HELM_PREC_TF32 only: 0 = tcgen05/TMEM kernel where blocks have at
+                           most 256 rows, else mma.sync; 1 = always mma.sync */
 } helm_config;
 
 typedef struct {

@@ -129,6 +129,9 @@ struct helm_ctx {
     int* box_of = nullptr;
 
     // factors
+    void* ufac = nullptr;              // tcgen05 tile image of the factors (TF32)
+    int64_t* ufac_off = nullptr;       // byte offset per subdomain
+    int umma_mt = 0;                   // 128-row tiles per block (0: tcgen05 not used)
     void* fac = nullptr;
     size_t fac_bytes = 0;
     bool factored = false;
@@ -658,7 +661,7 @@ int auto_panel(const helm_ctx* c, int nrhs) {
         p = nrhs >= 16 ? 4 : nrhs >= 2 ? 2 : 1;
     }
     // register budget of solve_kernel: 8 complex64 or 4 complex128 columns per thread
-    int pmax = c->prec == HELM_PREC_F64 ? 4 : 8;
+    int pmax = c->prec == HELM_PREC_F64 ? 4 : c->prec == HELM_PREC_TF32 ? 16 : 8;
     if (c->nbp_max > 960) pmax = 2;  // two rows per thread (plane blocks)
     if (p > pmax) p = pmax;
     int q = 1;
@@ -704,7 +707,11 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
                                      c->an32, c->af32, c->tab32, b, nrhs, buf, rs, c->stream);
             }
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
-            if (c->prec == HELM_PREC_TF32)
+            if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
+                launch_solve_umma(t, nt, c->subs_d, c->umma_mt * 128, nrhs,
+                                  static_cast<const float*>(c->ufac), c->ufac_off, c->Pv32,
+                                  c->inva32, buf, rs, c->err_d, c->stream);
+            else if (c->prec == HELM_PREC_TF32)
                 launch_solve_tc(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
                                 static_cast<const float*>(c->fac), c->Pv32, c->inva32, buf, rs,
                                 c->err_d, c->stream);
@@ -993,9 +1000,28 @@ int helm_factor(helm_ctx* c) {
     else
         launch_factor_f32(c->subs_d, c->P.nsub, c->nbp_max, c->P, c->m32, c->an32, c->af32,
                           static_cast<float*>(c->fac), c->err_d, c->stream);
-    if (c->prec == HELM_PREC_TF32)
+    if (c->prec == HELM_PREC_TF32) {
         launch_round_tf32(static_cast<float*>(c->fac), (int64_t)(c->fac_bytes / sizeof(float)),
                           c->stream);
+        int nblk_max = 0;
+        for (const SubDesc& S : c->subs_h) nblk_max = std::max(nblk_max, S.nblk);
+        if (c->cfg.tc_kernel == 0 && umma_supported(nblk_max)) {
+            c->umma_mt = umma_tiles(nblk_max);
+            std::vector<int64_t> off;
+            int64_t tot = 0;
+            for (const SubDesc& S : c->subs_h) {
+                off.push_back(tot);
+                tot += umma_factor_bytes(S, c->umma_mt);
+            }
+            if (!c->ufac) {
+                CK(cudaMalloc(&c->ufac, (size_t)tot));
+                c->dev_bytes += (size_t)tot;
+                TRY(upload(&c->ufac_off, off.data(), off.size() * sizeof(int64_t), c));
+            }
+            launch_repack_umma(c->subs_d, c->subs_h, c->umma_mt, static_cast<const float*>(c->fac),
+                               c->ufac_off, static_cast<float*>(c->ufac), c->stream);
+        }
+    }
     CK(cudaGetLastError());
     int err = 0;
     CK(cudaMemcpyAsync(&err, c->err_d, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
@@ -1125,6 +1151,10 @@ int helm_subdomain_solve(helm_ctx* c, int s, int nrhs, const void* R, void* U, i
         launch_solve<double>(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
                              static_cast<const double*>(c->fac), c->Pv64, c->inva64,
                              static_cast<cplx<double>*>(wb), we, c->err_d, c->stream);
+    else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
+        launch_solve_umma(td, 1, c->subs_d, c->umma_mt * 128, nrhs,
+                          static_cast<const float*>(c->ufac), c->ufac_off, c->Pv32, c->inva32,
+                          static_cast<cplx<float>*>(wb), we, c->err_d, c->stream);
     else if (c->prec == HELM_PREC_TF32)
         launch_solve_tc(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
                         static_cast<const float*>(c->fac), c->Pv32, c->inva32,
@@ -1220,7 +1250,7 @@ int helm_profile_get(helm_ctx* c, helm_profile* out) {
 
 void helm_destroy(helm_ctx* c) {
     if (!c) return;
-    void* ptrs[] = {c->subs_d, c->g_alpha, c->m64, c->m32, c->an64, c->af64, c->an32, c->af32,
+    void* ptrs[] = {c->ufac, c->ufac_off, c->subs_d, c->g_alpha, c->m64, c->m32, c->an64, c->af64, c->an32, c->af32,
                     c->Pv64, c->inva64, c->Pv32, c->inva32, c->tab64, c->tab32, c->box_of,
                     c->fac, c->err_d, c->tasks_d, c->inc_d, c->node_buf_d, c->buf, c->bvec,
                     c->small_d, c->partial_d, c->scal_d};

@@ -164,6 +164,18 @@ void launch_solve_tc(const Task* tasks, int ntask, const SubDesc* subs, int nbp_
                      cplx<float>* buf, int64_t buf_rhs_stride, int* err, cudaStream_t st);
 void launch_round_tf32(float* x, int64_t count, cudaStream_t st);
 
+// tcgen05 (5th-generation tensor core) subdomain solve, k_solve_umma.cu.  The
+// factors are repacked into 128-byte-swizzled K-major tiles of 128 rows.
+int umma_tiles(int nblk_max);
+bool umma_supported(int nblk_max);
+int64_t umma_factor_bytes(const SubDesc& S, int mt);
+void launch_repack_umma(const SubDesc* subs_d, const std::vector<SubDesc>& subs_h, int mt,
+                        const float* fac, const int64_t* dst_off_d, float* dst, cudaStream_t st);
+void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
+                       const float* afac, const int64_t* afac_off, const cplx<float>* Pv,
+                       const cplx<float>* inva, cplx<float>* buf, int64_t rstride, int* err,
+                       cudaStream_t st);
+
 template <typename T>
 void launch_gather(const Task* tasks, int ntask, int64_t max_win, const SubDesc* subs,
                    const Incoming* inc, const DevProblem& P, const T* m, const cplx<T>* an,

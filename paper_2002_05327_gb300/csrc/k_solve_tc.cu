@@ -316,8 +316,10 @@ static TcGeom tc_geom(int nbp_max, int kpad, int mtiles, int MTW, int NT, size_t
     const int BS = 8 * NT + (NT > 1 ? 8 : 0);
     const size_t bmat_bytes = (size_t)2 * 2 * kpad * BS * sizeof(float);
     G.cq = std::max<int>(4, (int)((24 * 1024) / col_bytes) & ~3);
-    const size_t budget = 200 * 1024;
-    G.nstage = 6;
+    // as many bytes in flight as shared memory allows: the block stream is
+    // latency-bound per SM, so its rate grows with the depth of the ring
+    const size_t budget = 220 * 1024;
+    G.nstage = 12;
     while (G.nstage > 2 && G.nstage * G.cq * col_bytes + bmat_bytes + 256 > budget) --G.nstage;
     while (G.nstage * G.cq * col_bytes + bmat_bytes + 256 > budget && G.cq > 4) G.cq -= 4;
     *smem = G.nstage * G.cq * col_bytes + bmat_bytes + 16 * G.nstage + 16;
@@ -350,7 +352,7 @@ void launch_solve_tc(const Task* tasks, int ntask, const SubDesc* subs, int nbp_
 #define HELM_TC(NT_, MTW_) \
     launch_tc<NT_, MTW_>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, err, st)
     if (MTW == 1) {
-        if (wide) HELM_TC(2, 1); else HELM_TC(1, 1);
+        if (panel >= 16) HELM_TC(4, 1); else if (wide) HELM_TC(2, 1); else HELM_TC(1, 1);
     } else if (MTW == 2) {
         if (wide) HELM_TC(2, 2); else HELM_TC(1, 2);
     } else {

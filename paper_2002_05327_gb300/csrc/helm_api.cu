@@ -107,6 +107,8 @@ struct helm_ctx {
     SubDesc* subs_d = nullptr;
     int nbp_max = 0;
     int64_t max_win = 0;
+    int max_nw0 = 0;       // largest window extent along x
+    int max_lines12 = 0;   // largest number of x-lines (nw[1]*nw[2]) of a window
 
     // global problem
     cplx<double>* g_alpha = nullptr;  // per axis: nodes then faces
@@ -155,6 +157,8 @@ struct helm_ctx {
     int cap_vec_rhs = 0;
     std::vector<cplx<double>*> gm;  // GMRES vectors (each nrhs*Ng)
     int gm_rhs = 0;
+    cplx<double>** vptr_d = nullptr;  // device copies of the V_i and Z_i pointers
+    cplx<double>** zptr_d = nullptr;
     cplx<double>* small_d = nullptr;  // dots / coefficients
     cplx<double>* partial_d = nullptr;
     double* scal_d = nullptr;
@@ -257,6 +261,10 @@ int ensure_small(helm_ctx* c, size_t count) {
     CK(cudaMalloc(&c->small_d, count * sizeof(cplx<double>)));
     CK(cudaMalloc(&c->partial_d, count * 1024 * sizeof(cplx<double>)));
     CK(cudaMalloc(&c->scal_d, count * sizeof(double)));
+    if (!c->vptr_d) {
+        CK(cudaMalloc(&c->vptr_d, 64 * sizeof(void*)));
+        CK(cudaMalloc(&c->zptr_d, 64 * sizeof(void*)));
+    }
     c->small_cap = count;
     return HELM_OK;
 }
@@ -347,12 +355,13 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
     if (!(h > 0) || !(omega > 0)) return fail(HELM_ERR_ARG, "h and omega must be positive");
     if (pml->width < 1 || pml->power < 0 || !(pml->sigma0 >= 0))
         return fail(HELM_ERR_ARG, "invalid PML");
-    if (part->overlap < 1) return fail(HELM_ERR_ARG, "overlap must be >= 1");
+    if (part->overlap < 1 || part->overlap > 128) return fail(HELM_ERR_ARG, "overlap must be in 1..128");
     if (cfg) c->cfg = *cfg;
     c->prec = HELM_PREC_MIXED;
     if (cfg && (cfg->precision == HELM_PREC_F64 || cfg->precision == HELM_PREC_TF32))
         c->prec = cfg->precision;
     if (c->cfg.restart <= 0) c->cfg.restart = 30;
+    if (c->cfg.restart > 63) return fail(HELM_ERR_ARG, "restart must be at most 63");
     c->pml = *pml;
     c->W = part->sub_pml > 0 ? part->sub_pml : pml->width;
     DevProblem& P = c->P;
@@ -525,6 +534,8 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
         for (int j = 0; j <= S.nlines; ++j) ia.push_back(1.0 / af[S.face_off[slow] + j]);
         c->nbp_max = std::max(c->nbp_max, S.nbp);
         c->max_win = std::max(c->max_win, S.win_elems);
+        c->max_nw0 = std::max(c->max_nw0, S.nw[0]);
+        c->max_lines12 = std::max(c->max_lines12, S.nw[1] * S.nw[2]);
     }
     {
         auto a128 = to_c128(an), f128 = to_c128(af), p128 = to_c128(pv), i128 = to_c128(ia);
@@ -637,6 +648,7 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
                 inc_all.push_back(I);
             }
             t.in_cnt = (int)inc_all.size() - t.in_off;
+            if (t.in_cnt > 32) return fail(HELM_ERR_ARG, "more than 32 incoming transfers on a subdomain");
             c->levels[level[k]].push_back(t);
         }
     std::vector<Task> all_tasks;
@@ -693,7 +705,8 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
             {
                 ProfScope ps(c, HELM_K_GATHER, 1, gbytes);
                 launch_gather<double>(t, nt, c->max_win, c->subs_d, c->inc_d, c->P, c->m64,
-                                      c->an64, c->af64, c->tab64, b, nrhs, buf, rs, c->stream);
+                                      c->an64, c->af64, c->tab64, b, nrhs, buf, rs, c->max_nw0,
+                                      c->max_lines12, c->stream);
             }
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
             launch_solve<double>(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
@@ -704,7 +717,8 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
             {
                 ProfScope ps(c, HELM_K_GATHER, 1, gbytes);
                 launch_gather<float>(t, nt, c->max_win, c->subs_d, c->inc_d, c->P, c->m32,
-                                     c->an32, c->af32, c->tab32, b, nrhs, buf, rs, c->stream);
+                                     c->an32, c->af32, c->tab32, b, nrhs, buf, rs, c->max_nw0,
+                                     c->max_lines12, c->stream);
             }
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
             if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
@@ -861,19 +875,21 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
             // Then A z_k = sum_i (-h_i) v_i + |w| v_{k+1} with v_{k+1} = -w/|w|.
             { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_apply_A(c->P, c->gwin, c->m64, nullptr, Z(k), w, nrhs, c->stream); }
             std::vector<std::vector<cd>> hsum(nrhs, std::vector<cd>(k + 2, 0.0));
+            {
+                std::vector<cplx<double>*> vp(k + 1);
+                for (int i = 0; i <= k; ++i) vp[i] = V(i);
+                CK(cudaMemcpyAsync(c->vptr_d, vp.data(), vp.size() * sizeof(void*),
+                                   cudaMemcpyHostToDevice, c->stream));
+            }
             for (int pass = 0; pass < 2; ++pass) {
-                for (int i = 0; i <= k; ++i)
-                    { ProfScope ps_(c, HELM_K_KRYLOV, 2); launch_dots(V(i), 0, 1, w, Ng, nrhs, c->small_d + (size_t)i * nrhs,
-                                c->partial_d, nblk, c->stream); }
+                { ProfScope ps_(c, HELM_K_KRYLOV, 2); launch_mdots(c->vptr_d, k + 1, w, Ng, nrhs, c->small_d, c->partial_d, nblk, c->stream); }
                 CK(cudaMemcpyAsync(hd.data(), c->small_d, (size_t)(k + 1) * nrhs * 16,
                                    cudaMemcpyDeviceToHost, c->stream));
                 CK(cudaStreamSynchronize(c->stream));
                 for (int i = 0; i <= k; ++i)
                     for (int r = 0; r < nrhs; ++r)
                         hsum[r][i] += cd(hd[(size_t)i * nrhs + r].re, hd[(size_t)i * nrhs + r].im);
-                for (int i = 0; i <= k; ++i)
-                    { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_sub_combo(w, V(i), 0, 1, c->small_d + (size_t)i * nrhs, Ng, nrhs, -1.0,
-                                     c->stream); }
+                { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_mcombo(w, c->vptr_d, k + 1, c->small_d, Ng, nrhs, -1.0, c->stream); }
             }
             std::vector<double> wn(nrhs);
             TRY(norms(w, wn));
@@ -934,8 +950,13 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
         }
         CK(cudaMemcpyAsync(c->small_d, coef.data(), coef.size() * 16, cudaMemcpyHostToDevice,
                            c->stream));
-        for (int i = 0; i < k; ++i)
-            { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_sub_combo(x, Z(i), 0, 1, c->small_d + (size_t)i * nrhs, Ng, nrhs, 1.0, c->stream); }
+        if (k > 0) {
+            std::vector<cplx<double>*> zp(k);
+            for (int i = 0; i < k; ++i) zp[i] = Z(i);
+            CK(cudaMemcpyAsync(c->zptr_d, zp.data(), zp.size() * sizeof(void*),
+                               cudaMemcpyHostToDevice, c->stream));
+            { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_mcombo(x, c->zptr_d, k, c->small_d, Ng, nrhs, 1.0, c->stream); }
+        }
         CK(cudaStreamSynchronize(c->stream));
     }
     if (st) {
@@ -1253,7 +1274,7 @@ void helm_destroy(helm_ctx* c) {
     void* ptrs[] = {c->ufac, c->ufac_off, c->subs_d, c->g_alpha, c->m64, c->m32, c->an64, c->af64, c->an32, c->af32,
                     c->Pv64, c->inva64, c->Pv32, c->inva32, c->tab64, c->tab32, c->box_of,
                     c->fac, c->err_d, c->tasks_d, c->inc_d, c->node_buf_d, c->buf, c->bvec,
-                    c->small_d, c->partial_d, c->scal_d};
+                    c->small_d, c->partial_d, c->scal_d, c->vptr_d, c->zptr_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto* p : c->gm) cudaFree(p);

@@ -180,7 +180,8 @@ template <typename T>
 void launch_gather(const Task* tasks, int ntask, int64_t max_win, const SubDesc* subs,
                    const Incoming* inc, const DevProblem& P, const T* m, const cplx<T>* an,
                    const cplx<T>* af, const T* beta_tab, const cplx<double>* b, int nrhs,
-                   cplx<T>* buf, int64_t buf_rhs_stride, cudaStream_t st);
+                   cplx<T>* buf, int64_t buf_rhs_stride, int max_line, int max_lines,
+                   cudaStream_t st);
 
 template <typename T>
 void launch_assemble(const DevProblem& P, const SubDesc* subs, const int* box_of,
@@ -200,6 +201,11 @@ void launch_dots(const cplx<double>* V, int64_t vstride, int nv, const cplx<doub
 void launch_sub_combo(cplx<double>* w, const cplx<double>* V, int64_t vstride, int nv,
                       const cplx<double>* coef, int64_t n, int nrhs, double sign,
                       cudaStream_t st);  // w[c] += sign * sum_i coef[i*nrhs+c] V_i[c]
+// fused over nv vectors given as a device array of pointers (nv <= 64)
+void launch_mdots(const cplx<double>* const* V, int nv, const cplx<double>* w, int64_t n, int nrhs,
+                  cplx<double>* out, cplx<double>* partial, int nblk, cudaStream_t st);
+void launch_mcombo(cplx<double>* w, const cplx<double>* const* V, int nv, const cplx<double>* coef,
+                   int64_t n, int nrhs, double sign, cudaStream_t st);
 void launch_scale_vec(cplx<double>* v, const cplx<double>* src, const double* s, int64_t n,
                       int nrhs, cudaStream_t st);  // v[c] = src[c] * s[c]
 void launch_conj(cplx<double>* v, int64_t count, cudaStream_t st);

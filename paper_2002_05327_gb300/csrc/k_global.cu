@@ -37,35 +37,48 @@ void launch_scale_J(const DevProblem& P, const Win<double>& g, const cplx<double
     scale_J_kernel<<<grid, 256, 0, st>>>(P, g, f, b, nrhs, conj_in ? 1 : 0);
 }
 
+// One thread per grid node: the stencil (FP64 complex reciprocals) is formed
+// once and applied to every right-hand side.
 __global__ void apply_A_kernel(DevProblem P, Win<double> w, const double* __restrict__ m,
                                const cplx<double>* __restrict__ b,
-                               const cplx<double>* __restrict__ u, cplx<double>* r) {
+                               const cplx<double>* __restrict__ u, cplx<double>* __restrict__ r,
+                               int nrhs) {
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = blockIdx.y;
     if (k >= Ng) return;
     int g[3];
     unflat(k, P.N, g);
-    Stencil<double> st = stencil_at(w, P.ndim, g, 1.0 / (P.h * P.h), P.omega * P.omega, m[k]);
-    const cplx<double>* uc = u + (int64_t)c * Ng;
-    cplx<double> Au = st.diag * uc[k];
+    const Stencil<double> st = stencil_at(w, P.ndim, g, 1.0 / (P.h * P.h), P.omega * P.omega, m[k]);
+    int64_t off[6];
+    cplx<double> co[6];
+    int np = 0;
     int64_t stride = 1;
     for (int a = 0; a < P.ndim; ++a) {
-        if (g[a] + 1 < P.N[a]) Au = Au + st.cp[a] * uc[k + stride];
-        if (g[a] > 0) Au = Au + st.cm[a] * uc[k - stride];
+        if (g[a] + 1 < P.N[a]) {
+            off[np] = stride;
+            co[np++] = st.cp[a];
+        }
+        if (g[a] > 0) {
+            off[np] = -stride;
+            co[np++] = st.cm[a];
+        }
         stride *= P.N[a];
     }
-    cplx<double> out = cneg(Au);
-    if (b) out = out + b[(int64_t)c * Ng + k];
-    r[(int64_t)c * Ng + k] = out;
+    for (int c = 0; c < nrhs; ++c) {
+        const cplx<double>* uc = u + (int64_t)c * Ng + k;
+        cplx<double> Au = st.diag * uc[0];
+        for (int i = 0; i < np; ++i) Au = Au + co[i] * uc[off[i]];
+        cplx<double> out = cneg(Au);
+        if (b) out = out + b[(int64_t)c * Ng + k];
+        r[(int64_t)c * Ng + k] = out;
+    }
 }
 
 void launch_apply_A(const DevProblem& P, const Win<double>& g, const double* m,
                     const cplx<double>* b, const cplx<double>* u, cplx<double>* r, int nrhs,
                     cudaStream_t st) {
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
-    dim3 grid((unsigned)((Ng + 255) / 256), nrhs);
-    apply_A_kernel<<<grid, 256, 0, st>>>(P, g, m, b, u, r);
+    apply_A_kernel<<<(unsigned)((Ng + 255) / 256), 256, 0, st>>>(P, g, m, b, u, r, nrhs);
 }
 
 // ---- batched dots: out[i*nrhs + c] = sum_k conj(V_i[c][k]) w[c][k]
@@ -162,6 +175,81 @@ void launch_scale_vec(cplx<double>* v, const cplx<double>* src, const double* s,
 __global__ void conj_kernel(cplx<double>* v, int64_t count) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k < count) v[k].im = -v[k].im;
+}
+
+// ---- fused multi-vector kernels of classical Gram-Schmidt: one pass over w
+// and every V_i (V given as a device array of pointers)
+constexpr int kMaxV = 64;
+
+__global__ void mdots_partial_kernel(const cplx<double>* const* __restrict__ V, int nv,
+                                     const cplx<double>* __restrict__ w, int64_t n, int nrhs,
+                                     cplx<double>* partial, int nblk) {
+    __shared__ double sr[8][DOT_NT / 32], si[8][DOT_NT / 32];
+    const int blk = blockIdx.x, c = blockIdx.y, i0 = blockIdx.z * 8;
+    const int nvb = min(8, nv - i0);
+    const int64_t chunk = (n + nblk - 1) / nblk;
+    const int64_t k0 = (int64_t)blk * chunk, k1 = min(n, k0 + chunk);
+    const cplx<double>* wc = w + (int64_t)c * n;
+    double ar[8] = {0}, ai[8] = {0};
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += DOT_NT) {
+        const cplx<double> b = wc[k];
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (i < nvb) {
+                const cplx<double> a = V[i0 + i][(int64_t)c * n + k];
+                ar[i] += a.re * b.re + a.im * b.im;
+                ai[i] += a.re * b.im - a.im * b.re;
+            }
+        }
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        for (int o = 16; o > 0; o >>= 1) {
+            ar[i] += __shfl_down_sync(0xffffffffu, ar[i], o);
+            ai[i] += __shfl_down_sync(0xffffffffu, ai[i], o);
+        }
+        if (lane == 0) {
+            sr[i][wp] = ar[i];
+            si[i][wp] = ai[i];
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < nvb) {
+        const int i = threadIdx.x;
+        double r = 0, im = 0;
+        for (int q = 0; q < DOT_NT / 32; ++q) {
+            r += sr[i][q];
+            im += si[i][q];
+        }
+        partial[((int64_t)(i0 + i) * nrhs + c) * nblk + blk] = mk<double>(r, im);
+    }
+}
+
+void launch_mdots(const cplx<double>* const* V, int nv, const cplx<double>* w, int64_t n, int nrhs,
+                  cplx<double>* out, cplx<double>* partial, int nblk, cudaStream_t st) {
+    dim3 grid(nblk, nrhs, (nv + 7) / 8);
+    mdots_partial_kernel<<<grid, DOT_NT, 0, st>>>(V, nv, w, n, nrhs, partial, nblk);
+    int count = nv * nrhs;
+    dots_final_kernel<<<(count + 127) / 128, 128, 0, st>>>(partial, nblk, count, out);
+}
+
+// w[c] += sign * sum_i coef[i*nrhs+c] V_i[c]
+__global__ void mcombo_kernel(cplx<double>* w, const cplx<double>* const* __restrict__ V, int nv,
+                              const cplx<double>* __restrict__ coef, int64_t n, int nrhs,
+                              double sign) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int c = blockIdx.y;
+    if (k >= n) return;
+    cplx<double> acc = w[(int64_t)c * n + k];
+    for (int i = 0; i < nv; ++i) acc = acc + sign * (coef[i * nrhs + c] * V[i][(int64_t)c * n + k]);
+    w[(int64_t)c * n + k] = acc;
+}
+
+void launch_mcombo(cplx<double>* w, const cplx<double>* const* V, int nv, const cplx<double>* coef,
+                   int64_t n, int nrhs, double sign, cudaStream_t st) {
+    dim3 grid((unsigned)((n + 255) / 256), nrhs);
+    mcombo_kernel<<<grid, 256, 0, st>>>(w, V, nv, coef, n, nrhs, sign);
 }
 
 void launch_conj(cplx<double>* v, int64_t count, cudaStream_t st) {

@@ -673,7 +673,7 @@ int auto_panel(const helm_ctx* c, int nrhs) {
         p = nrhs >= 16 ? 4 : nrhs >= 2 ? 2 : 1;
     }
     // register budget of solve_kernel: 8 complex64 or 4 complex128 columns per thread
-    int pmax = c->prec == HELM_PREC_F64 ? 4 : c->prec == HELM_PREC_TF32 ? 16 : 8;
+    int pmax = c->prec == HELM_PREC_F64 ? 4 : c->prec == HELM_PREC_TF32 ? 32 : 8;
     if (c->nbp_max > 960) pmax = 2;  // two rows per thread (plane blocks)
     if (p > pmax) p = pmax;
     int q = 1;
@@ -722,7 +722,7 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
             }
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
             if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
-                launch_solve_umma(t, nt, c->subs_d, c->umma_mt * 128, nrhs,
+                launch_solve_umma(t, nt, c->subs_d, c->umma_mt * 128, nrhs, panel,
                                   static_cast<const float*>(c->ufac), c->ufac_off, c->Pv32,
                                   c->inva32, buf, rs, c->err_d, c->stream);
             else if (c->prec == HELM_PREC_TF32)
@@ -1173,7 +1173,7 @@ int helm_subdomain_solve(helm_ctx* c, int s, int nrhs, const void* R, void* U, i
                              static_cast<const double*>(c->fac), c->Pv64, c->inva64,
                              static_cast<cplx<double>*>(wb), we, c->err_d, c->stream);
     else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
-        launch_solve_umma(td, 1, c->subs_d, c->umma_mt * 128, nrhs,
+        launch_solve_umma(td, 1, c->subs_d, c->umma_mt * 128, nrhs, panel,
                           static_cast<const float*>(c->ufac), c->ufac_off, c->Pv32, c->inva32,
                           static_cast<cplx<float>*>(wb), we, c->err_d, c->stream);
     else if (c->prec == HELM_PREC_TF32)

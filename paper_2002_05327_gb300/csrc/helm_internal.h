@@ -172,9 +172,9 @@ int64_t umma_factor_bytes(const SubDesc& S, int mt);
 void launch_repack_umma(const SubDesc* subs_d, const std::vector<SubDesc>& subs_h, int mt,
                         const float* fac, const int64_t* dst_off_d, float* dst, cudaStream_t st);
 void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
-                       const float* afac, const int64_t* afac_off, const cplx<float>* Pv,
-                       const cplx<float>* inva, cplx<float>* buf, int64_t rstride, int* err,
-                       cudaStream_t st);
+                       int panel, const float* afac, const int64_t* afac_off,
+                       const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf,
+                       int64_t rstride, int* err, cudaStream_t st);
 
 template <typename T>
 void launch_gather(const Task* tasks, int ntask, int64_t max_win, const SubDesc* subs,

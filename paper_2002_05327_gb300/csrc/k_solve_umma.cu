@@ -16,14 +16,17 @@
 //     whole K chunk of every M tile is one contiguous span for cp.async.bulk.
 //   * B: built in shared memory by the epilogue threads, [K chunk][N rows][128 B].
 //
-// Roles (one CTA per (task, panel of PG = 8 right-hand sides), N = 16):
-//   warps 0 .. 4*MT-1   epilogue: thread = one row p of an M tile; reads its row
-//                       of the accumulator from TMEM (tcgen05.ld), stores y or u,
-//                       and writes row p of the next B
-//   warp 4*MT           producer: bulk copies of A chunks into a ring of stages
-//   warp 4*MT+1         TMEM allocation; lane 0 issues the MMAs and commits
+// Roles (one CTA per (task, panel of PG right-hand sides, 128-row M tile);
+// the CTAs of the M tiles of a block form a thread-block cluster, N = 2 PG):
+//   warps 0-3   epilogue: thread = one block row p; reads its row of the
+//               accumulator from TMEM (tcgen05.ld), stores y or u, and writes
+//               row p of the next B into every CTA of the cluster (DSMEM)
+//   warp 4      producer: bulk copies of this CTA's A tile, chunk by chunk,
+//               into a ring deep enough to hold most of a line
+//   warp 5      TMEM allocation; lane 0 issues the MMAs and commits
 // Handshakes are mbarriers: full/empty per stage (TMA bytes / tcgen05.commit),
-// acc_full per step (tcgen05.commit), b_ready per step (epilogue threads).
+// acc_full per step (tcgen05.commit), b_ready per step (the epilogue threads
+// of every CTA of the cluster, remote arrivals with release semantics).
 // Every wait is bounded; on expiry the CTA raises the device error word, each
 // role leaves its loop, outstanding copies and MMAs are drained (bounded),
 // and TMEM is freed before the CTA exits.
@@ -43,15 +46,27 @@ __device__ __forceinline__ void mb_expect_tx(uint32_t bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
                  : "memory");
 }
-__device__ __forceinline__ void mb_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
 __device__ __forceinline__ bool mb_wait(uint32_t bar, uint32_t parity, uint32_t limit) {
     uint32_t done = 0;
     for (uint32_t it = 0; it < limit; ++it) {
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(bar), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+// Bounded wait with cluster-scope acquire: pairs with remote release arrivals.
+__device__ __forceinline__ bool mb_wait_cluster(uint32_t bar, uint32_t parity, uint32_t limit) {
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < limit; ++it) {
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
             : "r"(bar), "r"(parity)
@@ -122,11 +137,8 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
 }
 
 constexpr uint32_t kWait = 1u << 22;
-constexpr int kPG = 8;             // right-hand sides per CTA
-constexpr int kN = 2 * kPG;        // real columns
 constexpr int kChunkK = 32;        // K values per 128-byte row
 constexpr int kTileBytes = 128 * 128;  // 128 rows x 128 B
-constexpr int kBChunkBytes = kN * 128;  // B rows of one K chunk
 
 }  // namespace
 
@@ -171,44 +183,77 @@ __global__ void repack_umma_kernel(const SubDesc* __restrict__ subs, const float
     dst[dst_off[sub] / 4 + i] = __uint_as_float(to_tf32(v));  // dst_off in bytes
 }
 
-template <int MT>
-__global__ void __launch_bounds__(32 * (4 * MT + 2)) solve_umma_kernel(
-    const Task* __restrict__ tasks, const SubDesc* __restrict__ subs, int nrhs,
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t map_peer(uint32_t saddr, uint32_t rank) {
+    uint32_t r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ void st_cluster_v2(uint32_t addr, float a, float b) {
+    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(a), "f"(b) : "memory");
+}
+__device__ __forceinline__ void mb_arrive_cluster(uint32_t addr) {
+    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// One CTA per (task, panel of PG right-hand sides, 128-row M tile); the CTAs
+// of the M tiles of one block form a cluster of CR (1 or 2).  Each CTA streams
+// and multiplies only its own tile of D_j, holds the whole K extent of B, and
+// its epilogue writes the B rows of its block rows into every CTA of the
+// cluster (distributed shared memory) and arrives on every CTA's b_ready.
+// B is double-buffered: a peer may be one step ahead.
+constexpr int kIssuers = 4;  // MMA-issuing warps; K chunks are dealt round-robin to them
+
+template <int PG>
+__global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
+    const Task* __restrict__ tasks, const SubDesc* __restrict__ subs, int nrhs, int CR,
     const float* __restrict__ afac, const int64_t* __restrict__ afac_off,
     const cplx<float>* __restrict__ Pv, const cplx<float>* __restrict__ inva, cplx<float>* buf,
     int64_t rstride, int nstage, int* err) {
+    constexpr int kN = 2 * PG;              // real columns
+    constexpr int kBChunkBytes = kN * 128;  // B rows of one K chunk
     extern __shared__ __align__(1024) unsigned char smem_raw[];
-    const Task tk = tasks[blockIdx.x];
+    const uint32_t rank = CR > 1 ? cluster_rank() : 0;
+    const Task tk = tasks[blockIdx.x / CR];
     const SubDesc& S = subs[tk.sub];
     const int n = S.nblk, nl = S.nlines;
     int nkc;
-    const int64_t line_bytes = umma_line_bytes(n, MT, &nkc);
+    const int64_t line_bytes = umma_line_bytes(n, CR, &nkc);
     const int NS = nstage;
-    const uint32_t chunk_bytes = (uint32_t)(MT * kTileBytes);
     const uint32_t bbuf_bytes = (uint32_t)(nkc * kBChunkBytes);
 
-    // shared layout (1024-aligned): stages | B[2] | barriers | tmem slot | flags
+    // shared layout (1024-aligned): stages | B[2] | barriers | tmem slot | flag
     const uint32_t base = (su32(smem_raw) + 1023u) & ~1023u;
     unsigned char* gbase = smem_raw + (base - su32(smem_raw));
     const uint32_t stage0 = base;
-    const uint32_t b0 = stage0 + NS * chunk_bytes;
-    float* bgen = reinterpret_cast<float*>(gbase + NS * chunk_bytes);  // generic view of B[2]
+    const uint32_t b0 = stage0 + NS * kTileBytes;
+    float* bgen = reinterpret_cast<float*>(gbase + NS * kTileBytes);
     const uint32_t bars = b0 + 2 * bbuf_bytes;
-    uint64_t* bars_g = reinterpret_cast<uint64_t*>(gbase + NS * chunk_bytes + 2 * bbuf_bytes);
-    // barrier indices: full[NS], empty[NS], acc_full, b_ready, drain
+    uint64_t* bars_g = reinterpret_cast<uint64_t*>(gbase + NS * kTileBytes + 2 * bbuf_bytes);
     auto full = [&](int s) { return bars + 8u * s; };
     auto empty = [&](int s) { return bars + 8u * (NS + s); };
     const uint32_t acc_full = bars + 8u * (2 * NS);
-    const uint32_t b_ready = bars + 8u * (2 * NS + 1);
-    const uint32_t drain = bars + 8u * (2 * NS + 2);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars_g + 2 * NS + 3);
+    // b_ready of step s is barrier s & 1: arrivals of consecutive steps never
+    // share a phase (a count-based phase cannot tell the steps apart, and a
+    // peer CTA may arrive for step s+1 before this CTA's last step-s arrival)
+    auto b_ready = [&](int step) { return bars + 8u * (2 * NS + 1 + (step & 1)); };
+    const uint32_t drain = bars + 8u * (2 * NS + 3);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars_g + 2 * NS + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int NEPI = 4 * MT;  // epilogue warps
     const int nsteps = 2 * nl - 1;
     const int total_chunks = nsteps * nkc;
-    constexpr uint32_t kCols = (MT * kN) <= 32 ? 32 : (MT * kN) <= 64 ? 64 : (MT * kN) <= 128 ? 128 : 256;
+    // one accumulator of kN columns per issuer
+    constexpr uint32_t kCols = kIssuers * kN <= 32 ? 32 : kIssuers * kN <= 64 ? 64 :
+                               kIssuers * kN <= 128 ? 128 : 256;
 
     if (tid == 0) {
         *abort_flag = 0;
@@ -216,14 +261,18 @@ __global__ void __launch_bounds__(32 * (4 * MT + 2)) solve_umma_kernel(
             mb_init(full(s), 1);
             mb_init(empty(s), 1);
         }
-        mb_init(acc_full, 1);
-        mb_init(b_ready, NEPI * 32);
-        mb_init(drain, 1);
+        mb_init(acc_full, kIssuers);
+        mb_init(b_ready(0), 128 * CR);  // every epilogue thread of every CTA of the cluster
+        mb_init(b_ready(1), 128 * CR);
+        mb_init(drain, kIssuers);  // completes once every issuer's MMAs have
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // zero both B buffers (K rows beyond 2*roundup4(n) must stay zero)
     for (uint32_t i = tid; i < 2 * bbuf_bytes / 4; i += blockDim.x) bgen[i] = 0.f;
-    if (warp == NEPI + 1) {
+    {
+        float* sg = reinterpret_cast<float*>(gbase);
+        for (uint32_t i = tid; i < (uint32_t)NS * kTileBytes / 4; i += blockDim.x) sg[i] = 0.f;
+    }
+    if (warp == 5) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          su32(tmem_slot)),
                      "r"(kCols)
@@ -232,13 +281,18 @@ __global__ void __launch_bounds__(32 * (4 * MT + 2)) solve_umma_kernel(
     }
     tc_fence_before();
     __syncthreads();
+    if (CR > 1) cluster_sync();  // peers' barriers are initialised before any remote arrive
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == NEPI) {
+    if (warp == 4) {
         // ====================================================== producer
         if (lane == 0) {
             const char* abase = reinterpret_cast<const char*>(afac) + afac_off[tk.sub];
+            int rows = n - (int)rank * 128;
+            rows = rows < 8 ? 8 : ((rows + 7) & ~7);
+            if (rows > 128) rows = 128;
+            const uint32_t copy_bytes = (uint32_t)(rows * 128);
             int issued = 0;
             for (int i = 0; i < total_chunks; ++i) {
                 const int s = i % NS;
@@ -249,29 +303,36 @@ __global__ void __launch_bounds__(32 * (4 * MT + 2)) solve_umma_kernel(
                 if (*abort_flag) break;
                 const int step = i / nkc, kc = i % nkc;
                 const int j = step < nl ? step : 2 * nl - 2 - step;
-                mb_expect_tx(full(s), chunk_bytes);
-                bulk_g2s(stage0 + s * chunk_bytes,
-                         abase + (int64_t)j * line_bytes + (int64_t)kc * chunk_bytes, chunk_bytes,
-                         full(s));
+                mb_expect_tx(full(s), copy_bytes);
+                bulk_g2s(stage0 + s * kTileBytes,
+                         abase + (int64_t)j * line_bytes + ((int64_t)kc * CR + rank) * kTileBytes,
+                         copy_bytes, full(s));
                 issued = i + 1;
             }
             for (int i = (issued > NS ? issued - NS : 0); i < issued; ++i)
                 mb_wait(full(i % NS), (uint32_t)((i / NS) & 1), kWait);
         }
-    } else if (warp == NEPI + 1) {
-        // ====================================================== MMA issuer
+    } else if (warp >= 5 && warp < 5 + kIssuers) {
+        // ====================================================== MMA issuers
+        // issuer q takes the K chunks kc = q, q + kIssuers, ... of every line
+        // into its own accumulator (columns q*kN ...), so the per-instruction
+        // issue latency of the chunks overlaps across warps
+        const int q = warp - 5;
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_tf32(128, kN);
-            int ci = 0;
+            const uint32_t dacc = tmem + (uint32_t)(q * kN);
             for (int step = 0; step < nsteps && !*abort_flag; ++step) {
-                if (!mb_wait(b_ready, (uint32_t)(step & 1), kWait)) {
+                if (!mb_wait_cluster(b_ready(step), (uint32_t)((step >> 1) & 1), kWait)) {
                     atomicExch(err, 2);
                     *abort_flag = 1;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t bbuf = b0 + (step & 1) * bbuf_bytes;
-                for (int kc = 0; kc < nkc; ++kc, ++ci) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                const uint64_t bdesc0 = desc_sw128(b0 + (step & 1) * bbuf_bytes);
+                bool first = true;
+                for (int kc = q; kc < nkc; kc += kIssuers) {
+                    const int ci = step * nkc + kc;
                     const int s = ci % NS;
                     if (!mb_wait(full(s), (uint32_t)((ci / NS) & 1), kWait)) {
                         atomicExch(err, 2);
@@ -279,82 +340,115 @@ __global__ void __launch_bounds__(32 * (4 * MT + 2)) solve_umma_kernel(
                         break;
                     }
                     tc_fence_after();
-                    const uint32_t astage = stage0 + s * chunk_bytes;
+                    const uint64_t adesc = desc_sw128(stage0 + s * kTileBytes);
+                    const uint64_t bdesc = bdesc0 + (uint64_t)(kc * (kBChunkBytes >> 4));
 #pragma unroll
-                    for (int m = 0; m < MT; ++m) {
-#pragma unroll
-                        for (int kk = 0; kk < 4; ++kk) {
-                            const uint64_t ad = desc_sw128(astage + m * kTileBytes + kk * 32);
-                            const uint64_t bd = desc_sw128(bbuf + kc * kBChunkBytes + kk * 32);
-                            umma_tf32(tmem + m * kN, ad, bd, idesc, (kc > 0 || kk > 0) ? 1u : 0u);
-                        }
-                    }
-                    umma_commit(empty(s));  // frees the stage when these MMAs finish
+                    for (int kk = 0; kk < 4; ++kk)
+                        umma_tf32(dacc, adesc + (uint64_t)(2 * kk), bdesc + (uint64_t)(2 * kk), idesc,
+                                  (first && kk == 0) ? 0u : 1u);
+                    first = false;
+                    umma_commit(empty(s));
                 }
                 if (*abort_flag) break;
+                // (an issuer without a chunk -- K shorter than kIssuers chunks -- commits
+                // nothing pending; the epilogue never reads its accumulator)
                 umma_commit(acc_full);
             }
-            // drain: a commit to its own barrier completes once every MMA issued
-            // so far has, so no MMA can touch TMEM or shared memory after exit
             umma_commit(drain);
             mb_wait(drain, 0u, kWait);
         }
     } else {
-        // ====================================================== epilogue
-        const int tile = warp / 4;
-        const int p = tile * 128 + (warp % 4) * 32 + lane;  // owned row
+        // ====================================================== epilogue (warps 0-3)
+        const int p = (int)rank * 128 + warp * 32 + lane;  // owned block row
         const bool rv = p < n;
         const int n4 = (n + 3) & ~3;
         const cplx<float> pvp = rv ? Pv[S.coup_off + p] : mk<float>(0, 0);
         const cplx<float>* ia = inva + S.inva_off;
         cplx<float>* V = buf + tk.buf_off;
-        const int c0 = blockIdx.y * kPG;
+        const int c0 = blockIdx.y * PG;
         int ncol = nrhs - c0;
-        if (ncol > kPG) ncol = kPG;
-        // write row p of B (buffer bb): B[2c+w][2p+part]
+        if (ncol > PG) ncol = PG;
+        const int k0 = 2 * p;  // B rows k0 (Re column) and k0+1 (Im column)
+        const int kcb = k0 / kChunkK, kkb = k0 % kChunkK;
+        // byte offset of B[row][k0] within a buffer (k0, k0+1 adjacent)
+        auto boff = [&](int row) -> uint32_t {
+            const int chunk = (kkb / 4) ^ (row % 8);
+            return (uint32_t)(kcb * kBChunkBytes + row * 128 + chunk * 16 + (kkb % 4) * 4);
+        };
+        uint32_t peer_b[2] = {b0, b0}, peer_ready[2] = {b_ready(0), b_ready(0)};
+#pragma unroll
+        for (int r = 0; r < 2; ++r)
+            if (r < CR) {
+                peer_b[r] = map_peer(b0, (uint32_t)r);
+                peer_ready[r] = map_peer(b_ready(0), (uint32_t)r);  // b_ready(1) is 8 bytes on
+            }
+        // write B rows k0, k0+1 for right-hand side c into buffer bb of every CTA
         auto put_b = [&](int bb, int c, cplx<float> v) {
-            const int k0 = 2 * p;  // even, k0 and k0+1 share a chunk
-            const int kc = k0 / kChunkK, kk = k0 % kChunkK;
-            float* B = bgen + bb * (bbuf_bytes / 4) + kc * (kBChunkBytes / 4);
             const float re = __uint_as_float(to_tf32(v.re)), im = __uint_as_float(to_tf32(v.im));
             const float nim = __uint_as_float(to_tf32(-v.im));
+            const uint32_t o0 = (uint32_t)bb * bbuf_bytes + boff(2 * c);
+            const uint32_t o1 = (uint32_t)bb * bbuf_bytes + boff(2 * c + 1);
 #pragma unroll
-            for (int w = 0; w < 2; ++w) {
-                const int row = 2 * c + w;
-                const int chunk = (kk / 4) ^ (row % 8);
-                float* e = B + row * 32 + chunk * 4 + (kk % 4);
-                e[0] = w == 0 ? re : im;    // k = 2p   (Re D column)
-                e[1] = w == 0 ? nim : re;   // k = 2p+1 (Im D column)
-            }
+            for (int r = 0; r < 2; ++r)
+                if (r < CR) {
+                    st_cluster_v2(peer_b[r] + o0, re, nim);  // row 2c:   Re r, -Im r
+                    st_cluster_v2(peer_b[r] + o1, im, re);   // row 2c+1: Im r,  Re r
+                }
         };
-        cplx<float> pre[kPG];
-        // step 0 operand: b_0
+        auto signal = [&](int step) {  // B of `step` is written everywhere
+            asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+            tc_fence_before();
 #pragma unroll
-        for (int c = 0; c < kPG; ++c) {
+            for (int r = 0; r < 2; ++r)
+                if (r < CR) mb_arrive_cluster(peer_ready[r] + 8u * (step & 1));
+        };
+        // operand needed after the product of step s: b_{j+1} (forward line j)
+        // or y_j (backward line j); loaded one whole step ahead
+        auto operand_line = [&](int step) -> int {
+            if (step >= nsteps) return -1;
+            if (step < nl) return step + 1 < nl ? step + 1 : -1;
+            return 2 * nl - 2 - step;
+        };
+        auto load_operand = [&](int step, cplx<float> (&dst)[PG]) {
+            const int jj = operand_line(step);
+#pragma unroll
+            for (int c = 0; c < PG; ++c)
+                dst[c] = (rv && c < ncol && jj >= 0) ? V[(int64_t)(c0 + c) * rstride + (int64_t)jj * n + p]
+                                                     : mk<float>(0, 0);
+        };
+        cplx<float> pre[PG], pre_next[PG], outv[PG];
+#pragma unroll
+        for (int c = 0; c < PG; ++c) {
             cplx<float> b = (rv && c < ncol) ? V[(int64_t)(c0 + c) * rstride + p] : mk<float>(0, 0);
             if (p < n4) put_b(0, c, b);
         }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        tc_fence_before();
-        mb_arrive(b_ready);
+        load_operand(0, pre);
+        signal(0);
         for (int step = 0; step < nsteps; ++step) {
             const bool fwd = step < nl;
             const int j = fwd ? step : 2 * nl - 2 - step;
-            const int jj = fwd ? j + 1 : j;
-#pragma unroll
-            for (int c = 0; c < kPG; ++c)
-                pre[c] = (rv && c < ncol && jj < nl) ? V[(int64_t)(c0 + c) * rstride + (int64_t)jj * n + p]
-                                                     : mk<float>(0, 0);
+            load_operand(step + 1, pre_next);
             bool bad = *abort_flag || !mb_wait(acc_full, (uint32_t)(step & 1), kWait);
-            // the whole warp must agree before the warp-collective tcgen05.ld
-            if (__any_sync(0xffffffffu, bad)) {
+            if (__any_sync(0xffffffffu, bad)) {  // warp-uniform before the collective load
                 atomicExch(err, 2);
                 *abort_flag = 1;
                 break;
             }
             tc_fence_after();
-            float acc[16];
-            tmem_ld16(tmem + ((uint32_t)((warp % 4) * 32) << 16) + tile * kN, acc);
+            float acc[kN];
+#pragma unroll
+            for (int e = 0; e < kN; ++e) acc[e] = 0.f;
+#pragma unroll
+            for (int iq = 0; iq < kIssuers; ++iq) {
+                if (iq >= nkc) break;  // issuers without a chunk hold no partial sum
+#pragma unroll
+                for (int q = 0; q < kN / 16; ++q) {
+                    float part[16];
+                    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + iq * kN + 16 * q, part);
+#pragma unroll
+                    for (int e = 0; e < 16; ++e) acc[16 * q + e] += part[e];
+                }
+            }
             cplx<float> coup = mk<float>(0, 0);
             if (rv) {
                 if (fwd && j + 1 < nl) coup = pvp * ia[j + 1];   // a_{j+1}
@@ -363,23 +457,27 @@ __global__ void __launch_bounds__(32 * (4 * MT + 2)) solve_umma_kernel(
             }
             const int nb = (step + 1) & 1;
 #pragma unroll
-            for (int c = 0; c < kPG; ++c) {
+            for (int c = 0; c < PG; ++c) {
                 const cplx<float> y = mk<float>(acc[2 * c], acc[2 * c + 1]);
-                const cplx<float> out = fwd ? y : pre[c] - y;
-                if (rv && c < ncol) V[(int64_t)(c0 + c) * rstride + (int64_t)j * n + p] = out;
+                outv[c] = fwd ? y : pre[c] - y;
                 cplx<float> nbv = mk<float>(0, 0);
-                if (rv) nbv = (fwd && j + 1 < nl) ? pre[c] - coup * out : coup * out;
+                if (rv) nbv = (fwd && j + 1 < nl) ? pre[c] - coup * outv[c] : coup * outv[c];
                 if (step + 1 < nsteps && p < n4) put_b(nb, c, nbv);
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            tc_fence_before();
-            if (step + 1 < nsteps) mb_arrive(b_ready);
+            if (step + 1 < nsteps) signal(step + 1);
+            // global stores after the release-arrive, so it does not wait for them
+#pragma unroll
+            for (int c = 0; c < PG; ++c) {
+                if (rv && c < ncol) V[(int64_t)(c0 + c) * rstride + (int64_t)j * n + p] = outv[c];
+                pre[c] = pre_next[c];
+            }
         }
     }
     tc_fence_before();
     __syncthreads();
+    if (CR > 1) cluster_sync();  // no CTA leaves while a peer may still write into it
     tc_fence_after();
-    if (warp == NEPI + 1)
+    if (warp == 5)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
                      : "memory");
 }
@@ -397,37 +495,47 @@ int umma_tiles(int nblk_max) { return (nblk_max + 127) / 128; }
 
 int64_t umma_factor_bytes(const SubDesc& S, int mt) { return umma_line_bytes(S.nblk, mt, nullptr) * S.nlines; }
 
-template <int MT>
-static void launch_mt(const Task* tasks, int ntask, const SubDesc* subs, int nkc_max, int nrhs,
-                      const float* afac, const int64_t* afac_off, const cplx<float>* Pv,
+template <int PG>
+static void launch_pg(const Task* tasks, int ntask, const SubDesc* subs, int CR, int nkc_max,
+                      int nrhs, const float* afac, const int64_t* afac_off, const cplx<float>* Pv,
                       const cplx<float>* inva, cplx<float>* buf, int64_t rstride, int* err,
                       cudaStream_t st) {
-    const size_t chunk = (size_t)MT * kTileBytes;
-    const size_t bbuf = (size_t)nkc_max * kBChunkBytes;
-    const size_t fixed = 2 * bbuf + 8 * 64 + 64 + 1024;  // B buffers, barriers, slots, alignment
-    int ns = (int)std::min<size_t>(8, (220 * 1024 - fixed) / chunk);
+    const size_t bbuf = (size_t)nkc_max * 2 * PG * 128;
+    const size_t fixed = 2 * bbuf + 8 * 64 + 64 + 1024;  // B[2], barriers, slots, alignment
+    int ns = (int)std::min<size_t>(16, (224 * 1024 - fixed) / kTileBytes);
     if (ns < 2) ns = 2;
-    const size_t smem = ns * chunk + fixed;
-    cudaFuncSetAttribute(solve_umma_kernel<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(ntask, (nrhs + kPG - 1) / kPG);
-    solve_umma_kernel<MT><<<grid, 32 * (4 * MT + 2), smem, st>>>(tasks, subs, nrhs, afac, afac_off, Pv,
-                                                                 inva, buf, rstride, ns, err);
+    const size_t smem = ns * (size_t)kTileBytes + fixed;
+    cudaFuncSetAttribute(solve_umma_kernel<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ntask * CR, (nrhs + PG - 1) / PG, 1);
+    cfg.blockDim = dim3(32 * (5 + kIssuers), 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = CR;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, solve_umma_kernel<PG>, tasks, subs, nrhs, CR, afac, afac_off, Pv, inva,
+                       buf, rstride, ns, err);
 }
 
 bool umma_supported(int nblk_max) { return umma_tiles(nblk_max) <= 2; }
 
 void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
-                       const float* afac, const int64_t* afac_off, const cplx<float>* Pv,
-                       const cplx<float>* inva, cplx<float>* buf, int64_t rstride, int* err,
-                       cudaStream_t st) {
+                       int panel, const float* afac, const int64_t* afac_off,
+                       const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf,
+                       int64_t rstride, int* err, cudaStream_t st) {
     if (ntask == 0) return;
-    const int mt = umma_tiles(nblk_max);
+    const int CR = umma_tiles(nblk_max);  // cluster of one CTA per 128-row tile
     int nkc = 0;
-    umma_line_bytes(nblk_max, mt, &nkc);
-    if (mt <= 1)
-        launch_mt<1>(tasks, ntask, subs, nkc, nrhs, afac, afac_off, Pv, inva, buf, rstride, err, st);
-    else
-        launch_mt<2>(tasks, ntask, subs, nkc, nrhs, afac, afac_off, Pv, inva, buf, rstride, err, st);
+    umma_line_bytes(nblk_max, CR, &nkc);
+#define HELM_UMMA(PG_) \
+    launch_pg<PG_>(tasks, ntask, subs, CR, nkc, nrhs, afac, afac_off, Pv, inva, buf, rstride, err, st)
+    if (panel >= 32) HELM_UMMA(32); else if (panel >= 16) HELM_UMMA(16); else HELM_UMMA(8);
+#undef HELM_UMMA
 }
 
 }  // namespace helm

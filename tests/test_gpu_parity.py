@@ -59,6 +59,9 @@ CASES = {
     "2d-layered-4x3-5rhs": lambda: W.small_2d(nx=60, ny=52, nbx=4, nby=3, nrhs=5),
     "2d-1x1": lambda: W.small_2d(nx=30, ny=26, nbx=1, nby=1, nrhs=1),
     "2d-strip-3x1": lambda: W.small_2d(nx=45, ny=20, nbx=3, nby=1, nrhs=2),
+    # blocks of more than 128 rows: the tensor-core solve runs as a 2-CTA cluster
+    "2d-wide-2x2": lambda: W.small_2d(nx=260, ny=48, nbx=2, nby=2, pml=8, overlap=4, sub_pml=8,
+                                      nrhs=10),
     "3d-const-2x2x2": lambda: W.small_3d(),
     "3d-layered-3x2x2": lambda: W.small_3d(n=(27, 18, 16), nb=(3, 2, 2), nrhs=1, medium="layered"),
 }
@@ -192,4 +195,16 @@ def test_deterministic_and_device_pointers(H):
     assert np.array_equal(u1, u2)
     ud = H.helm_apply_ddm(ctx, torch.from_numpy(wl.f).cuda())
     assert np.array_equal(ud.cpu().numpy(), u1)
+    ctx.close()
+
+
+def test_cluster_tensor_core_path_is_deterministic(H):
+    """Blocks of more than 128 rows run as 2-CTA clusters exchanging the B
+    operand through distributed shared memory; repeated applications must be
+    bitwise identical (a handshake race would show as run-to-run changes)."""
+    wl = CASES["2d-wide-2x2"]()
+    ctx = _ctx(H, wl, 2)
+    u1 = H.helm_apply_ddm(ctx, wl.f)
+    for _ in range(3):
+        assert np.array_equal(H.helm_apply_ddm(ctx, wl.f), u1)
     ctx.close()

@@ -104,6 +104,14 @@ typedef struct {
     int32_t profile;    /* 1: time every kernel launch with CUDA events (helm_profile_get) */
     int32_t tc_kernel;  /* HELM_PREC_TF32 only: 0 = tcgen05/TMEM kernel where blocks have at
                            most 256 rows, else mma.sync; 1 = always mma.sync */
+    int32_t wait_limit; /* bound of every ordinary spin-wait inside the subdomain-solve
+                           kernels (a bulk copy, an MMA commit, a peer CTA's handshake),
+                           in polls of the mbarrier: 0 = default (2^22 polls); n > 0 = n polls; -1 = no poll, so the first such wait
+                           gives up at once.  A wait that gives up makes the call return
+                           HELM_ERR_TIMEOUT; the kernel stops issuing work, still waits
+                           (with the default bound) for the copies and MMAs it has started,
+                           frees its tensor memory and exits, so the CUDA context stays
+                           usable.  -1 exists for testing callers' handling of that error. */
 } helm_config;
 
 typedef struct {

@@ -48,7 +48,7 @@ class helm_config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("rhs_panel", ctypes.c_int32),
                 ("restart", ctypes.c_int32), ("verbose", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("profile", ctypes.c_int32),
-                ("tc_kernel", ctypes.c_int32)]
+                ("tc_kernel", ctypes.c_int32), ("wait_limit", ctypes.c_int32)]
 
 
 KERNEL_CLASSES = ("factor", "solve", "gather", "assemble", "krylov")
@@ -195,7 +195,7 @@ class Context:
 def helm_setup(ndim, n, h, omega, m, pml_width, sigma0, nb, overlap, power=2,
                form=HELM_PML_LITERAL, cuts=None, sub_pml=0, precision=HELM_PREC_MIXED,
                rhs_panel=0, restart=30, verbose=0, stream=None, profile=0,
-               tc_kernel=0) -> Context:
+               tc_kernel=0, wait_limit=0) -> Context:
     L = lib()
     nn = (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
     m = np.ascontiguousarray(m, dtype=np.float64)
@@ -213,7 +213,8 @@ def helm_setup(ndim, n, h, omega, m, pml_width, sigma0, nb, overlap, power=2,
     part.overlap = int(overlap)
     part.sub_pml = int(sub_pml)
     cfg = helm_config(int(precision), int(rhs_panel), int(restart), int(verbose),
-                      ctypes.c_void_p(stream) if stream else None, int(profile), int(tc_kernel))
+                      ctypes.c_void_p(stream) if stream else None, int(profile), int(tc_kernel),
+                      int(wait_limit))
     out = ctypes.c_void_p()
     _check(L.helm_setup(ctypes.byref(out), int(ndim), nn, float(h), float(omega),
                         m.ctypes.data_as(ctypes.c_void_p), ctypes.byref(pml), ctypes.byref(part),
@@ -342,5 +343,63 @@ def helm_profile_get(ctx: Context) -> dict:
     return out.as_dict()
 
 
+# ----------------------------------------------------------------------------- autograd
+def _make_helm_solve():
+    import torch
+
+    class HelmSolve(torch.autograd.Function):
+        """U = A(m)^{-1} J F for a squared slowness m on the full grid, with the
+        gradient of any real loss of U with respect to m (Remark 2: the
+        adjoint-state gradient that full waveform inversion uses).
+
+        forward(m, F, spec, rtol, maxit): m is a float64 tensor of the full grid
+        (copied to the host for helm_setup); F a CUDA complex128 tensor
+        [nrhs, *grid]; spec the keyword arguments of helm_setup other than m
+        (ndim, n, h, omega, pml_width, sigma0, nb, overlap, ...).  It sets up
+        and factors a context for this m, solves with helm_solve and keeps the
+        context for the backward pass.
+
+        backward(gU), with gU = dL/dRe U + i dL/dIm U (torch's convention for
+        complex tensors): lam = A^{-H} gU by helm_adjoint on the same factors,
+        then dL/dm = -omega^2 sum_s Re(conj(lam_s) J u_s) by helm_gradient.
+        F is not differentiated (its gradient is None)."""
+
+        @staticmethod
+        def forward(actx, m, F, spec, rtol=1e-8, maxit=100):
+            mh = m.detach().to("cpu", torch.float64).numpy()
+            helm = helm_setup(m=mh, **spec)
+            helm_factor(helm)
+            U, _ = helm_solve(helm, F.detach().contiguous(), rtol, maxit)
+            actx.helm, actx.rtol, actx.maxit = helm, rtol, maxit
+            actx.m_meta = (m.device, m.dtype)
+            actx.save_for_backward(U)
+            return U
+
+        @staticmethod
+        def backward(actx, gU):
+            (U,) = actx.saved_tensors
+            lam, _ = helm_adjoint(actx.helm, gU.contiguous(), actx.rtol, actx.maxit)
+            g = helm_gradient(actx.helm, U, lam)
+            dev, dt = actx.m_meta
+            return g.to(dev, dt), None, None, None, None
+
+    return HelmSolve
+
+
+_helm_solve_cls = None
+
+
+def __getattr__(name):
+    """``HelmSolve`` (a torch.autograd.Function) is built on first access so that
+    importing this module does not import torch:
+    ``U = paper_2002_05327_gb300.HelmSolve.apply(m, F, spec, rtol, maxit)``."""
+    global _helm_solve_cls
+    if name == "HelmSolve":
+        if _helm_solve_cls is None:
+            _helm_solve_cls = _make_helm_solve()
+        return _helm_solve_cls
+    raise AttributeError(name)
+
+
 __all__ = [n for n in dir() if n.startswith("helm_") or n.startswith("HELM_")] + [
-    "Context", "HelmError", "lib", "LIB_PATH"]
+    "Context", "HelmError", "HelmSolve", "lib", "LIB_PATH"]

@@ -139,6 +139,7 @@ struct helm_ctx {
     bool factored = false;
     double t_factor_ms = 0;
     int* err_d = nullptr;
+    uint32_t wait_polls = kDefaultWaitPolls;  // ordinary bounded waits of the solve kernels
 
     // schedule
     std::vector<std::vector<Task>> levels;
@@ -362,6 +363,10 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
         c->prec = cfg->precision;
     if (c->cfg.restart <= 0) c->cfg.restart = 30;
     if (c->cfg.restart > 63) return fail(HELM_ERR_ARG, "restart must be at most 63");
+    if (c->cfg.wait_limit < -1) return fail(HELM_ERR_ARG, "wait_limit must be -1, 0 or positive");
+    c->wait_polls = c->cfg.wait_limit == 0    ? kDefaultWaitPolls
+                    : c->cfg.wait_limit == -1 ? 0u
+                                              : (uint32_t)c->cfg.wait_limit;
     c->pml = *pml;
     c->W = part->sub_pml > 0 ? part->sub_pml : pml->width;
     DevProblem& P = c->P;
@@ -711,7 +716,7 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
             launch_solve<double>(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
                                  static_cast<const double*>(c->fac), c->Pv64, c->inva64, buf, rs,
-                                 c->err_d, c->stream);
+                                 DevStatus{c->err_d, c->wait_polls}, c->stream);
         } else {
             auto* buf = static_cast<cplx<float>*>(c->buf);
             {
@@ -724,15 +729,15 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
             if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
                 launch_solve_umma(t, nt, c->subs_d, c->umma_mt * 128, nrhs, panel,
                                   static_cast<const float*>(c->ufac), c->ufac_off, c->Pv32,
-                                  c->inva32, buf, rs, c->err_d, c->stream);
+                                  c->inva32, buf, rs, DevStatus{c->err_d, c->wait_polls}, c->stream);
             else if (c->prec == HELM_PREC_TF32)
                 launch_solve_tc(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
                                 static_cast<const float*>(c->fac), c->Pv32, c->inva32, buf, rs,
-                                c->err_d, c->stream);
+                                DevStatus{c->err_d, c->wait_polls}, c->stream);
             else
                 launch_solve<float>(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
                                     static_cast<const float*>(c->fac), c->Pv32, c->inva32, buf,
-                                    rs, c->err_d, c->stream);
+                                    rs, DevStatus{c->err_d, c->wait_polls}, c->stream);
         }
     }
     ProfScope ps(c, HELM_K_ASSEMBLE, 1, (double)c->Ng * nrhs * 16.0);
@@ -893,6 +898,7 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
             }
             std::vector<double> wn(nrhs);
             TRY(norms(w, wn));
+            TRY(check_device_error(c));  // a timed-out preconditioner ends the solve here
             for (int r = 0; r < nrhs; ++r) sc[r] = wn[r] > 1e-300 ? -1.0 / wn[r] : 0.0;
             CK(cudaMemcpyAsync(c->scal_d, sc.data(), nrhs * 8, cudaMemcpyHostToDevice, c->stream));
             { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_scale_vec(V(k + 1), w, c->scal_d, Ng, nrhs, c->stream); }
@@ -1171,19 +1177,19 @@ int helm_subdomain_solve(helm_ctx* c, int s, int nrhs, const void* R, void* U, i
     if (c->prec == HELM_PREC_F64)
         launch_solve<double>(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
                              static_cast<const double*>(c->fac), c->Pv64, c->inva64,
-                             static_cast<cplx<double>*>(wb), we, c->err_d, c->stream);
+                             static_cast<cplx<double>*>(wb), we, DevStatus{c->err_d, c->wait_polls}, c->stream);
     else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
         launch_solve_umma(td, 1, c->subs_d, c->umma_mt * 128, nrhs, panel,
                           static_cast<const float*>(c->ufac), c->ufac_off, c->Pv32, c->inva32,
-                          static_cast<cplx<float>*>(wb), we, c->err_d, c->stream);
+                          static_cast<cplx<float>*>(wb), we, DevStatus{c->err_d, c->wait_polls}, c->stream);
     else if (c->prec == HELM_PREC_TF32)
         launch_solve_tc(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
                         static_cast<const float*>(c->fac), c->Pv32, c->inva32,
-                        static_cast<cplx<float>*>(wb), we, c->err_d, c->stream);
+                        static_cast<cplx<float>*>(wb), we, DevStatus{c->err_d, c->wait_polls}, c->stream);
     else
         launch_solve<float>(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
                             static_cast<const float*>(c->fac), c->Pv32, c->inva32,
-                            static_cast<cplx<float>*>(wb), we, c->err_d, c->stream);
+                            static_cast<cplx<float>*>(wb), we, DevStatus{c->err_d, c->wait_polls}, c->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->stream));
     if (c->prec == HELM_PREC_F64) {
@@ -1228,6 +1234,7 @@ int helm_subdomain_solve_noalloc(helm_ctx* c, int s, int nrhs, const void* R, vo
     a.R = static_cast<const cplx<double>*>(R);
     a.U = static_cast<cplx<double>*>(U);
     a.err = c->err_d;
+    a.polls = c->wait_polls;
     a.stream = c->stream;
     CK(noalloc_subdomain_solve(a));
     CK(cudaStreamSynchronize(c->stream));

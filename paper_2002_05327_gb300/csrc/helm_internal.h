@@ -152,16 +152,28 @@ void launch_factor_f64(const SubDesc* subs, int nsub, int nbp_max, const DevProb
                        const double* m64, const cplx<double>* an, const cplx<double>* af,
                        double* fac, int* err, cudaStream_t st);
 
-// err: device error word; set to 2 if a bounded wait for a bulk copy expired.
+// Error reporting and wait bounds of the solve kernels.  Every spin-wait in
+// them is bounded.  An ordinary wait (a copy, an MMA commit, a cluster
+// handshake the kernel needs to make progress) gives up after `polls` polls
+// (0: at once); the kernel then writes 2 to *err, stops issuing work and
+// drains what it already started.  The drain waits always use kDrainPolls,
+// so no CTA releases shared memory or TMEM while a copy or MMA still targets it.
+constexpr uint32_t kDrainPolls = 1u << 22;
+constexpr uint32_t kDefaultWaitPolls = 1u << 22;
+struct DevStatus {
+    int* err;        // device error word: 1 = numerical breakdown, 2 = a wait expired
+    uint32_t polls;  // polls of each ordinary wait
+};
+
 template <typename T>
 void launch_solve(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                   int panel, const T* fac, const cplx<T>* Pv, const cplx<T>* inva, cplx<T>* buf,
-                  int64_t buf_rhs_stride, int* err, cudaStream_t st);
+                  int64_t buf_rhs_stride, DevStatus ds, cudaStream_t st);
 
 // Tensor-core (TF32 mma, FP32 accumulate) variant for complex64 factors.
 void launch_solve_tc(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                      int panel, const float* fac, const cplx<float>* Pv, const cplx<float>* inva,
-                     cplx<float>* buf, int64_t buf_rhs_stride, int* err, cudaStream_t st);
+                     cplx<float>* buf, int64_t buf_rhs_stride, DevStatus ds, cudaStream_t st);
 void launch_round_tf32(float* x, int64_t count, cudaStream_t st);
 
 // tcgen05 (5th-generation tensor core) subdomain solve, k_solve_umma.cu.  The
@@ -174,7 +186,7 @@ void launch_repack_umma(const SubDesc* subs_d, const std::vector<SubDesc>& subs_
 void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
                        int panel, const float* afac, const int64_t* afac_off,
                        const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf,
-                       int64_t rstride, int* err, cudaStream_t st);
+                       int64_t rstride, DevStatus ds, cudaStream_t st);
 
 template <typename T>
 void launch_gather(const Task* tasks, int ntask, int64_t max_win, const SubDesc* subs,
@@ -224,6 +236,7 @@ struct NoAllocArgs {
     const cplx<double>* R;
     cplx<double>* U;
     int* err;
+    uint32_t polls;
     cudaStream_t stream;
 };
 size_t noalloc_capacity_bytes();

@@ -80,7 +80,7 @@ static cudaError_t run(const NoAllocArgs& a, void* scratch) {
     noalloc_pack<T><<<blocks, 256, 0, a.stream>>>(a.R, wb, count);
     launch_solve<T>(task, 1, a.subs, a.nbp_max, a.nrhs, a.panel, static_cast<const T*>(a.fac),
                     static_cast<const cplx<T>*>(a.Pv), static_cast<const cplx<T>*>(a.inva), wb,
-                    a.win_elems, a.err, a.stream);
+                    a.win_elems, DevStatus{a.err, a.polls}, a.stream);
     noalloc_unpack<T><<<blocks, 256, 0, a.stream>>>(wb, a.U, count);
     return cudaGetLastError();
 }

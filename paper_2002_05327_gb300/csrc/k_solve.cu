@@ -83,7 +83,7 @@ __device__ __forceinline__ bool consumers_sync_any(int nthreads, int flag) {
     return out != 0;
 }
 
-constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint32_t kWaitLimit = kDrainPolls;
 
 struct SolveGeom {
     int cq;       // columns per chunk
@@ -113,7 +113,7 @@ __global__ void __launch_bounds__(1024) solve_kernel(const Task* __restrict__ ta
                                                      const cplx<T>* __restrict__ Pv,
                                                      const cplx<T>* __restrict__ inva,
                                                      cplx<T>* buf, int64_t rstride, SolveGeom G,
-                                                     int nbp_max, int* err) {
+                                                     int nbp_max, DevStatus ds) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const Task tk = tasks[blockIdx.x];
     const SubDesc& S = subs[tk.sub];
@@ -147,8 +147,8 @@ __global__ void __launch_bounds__(1024) solve_kernel(const Task* __restrict__ ta
         int issued = 0;
         for (int i = 0; i < seq.total; ++i) {
             const int s = i % NS;
-            if (i >= NS && !mbar_wait(&empty[s], (uint32_t)(((i / NS) - 1) & 1), kWaitLimit)) {
-                atomicExch(err, 2);
+            if (i >= NS && !mbar_wait(&empty[s], (uint32_t)(((i / NS) - 1) & 1), ds.polls)) {
+                atomicExch(ds.err, 2);
                 *abort_flag = 1;
             }
             if (*abort_flag) break;
@@ -204,8 +204,8 @@ __global__ void __launch_bounds__(1024) solve_kernel(const Task* __restrict__ ta
             for (int c = 0; c < PG; ++c) acc[r][c] = mk<T>(0, 0);
         for (int k = 0; k < seq.per_line; ++k, ++ci) {
             const int s = ci % NS;
-            if (!*abort_flag && !mbar_wait(&full[s], (uint32_t)((ci / NS) & 1), kWaitLimit)) {
-                atomicExch(err, 2);
+            if (!*abort_flag && !mbar_wait(&full[s], (uint32_t)((ci / NS) & 1), ds.polls)) {
+                atomicExch(ds.err, 2);
                 *abort_flag = 1;
             }
             const int q0 = seq.col0(ci);
@@ -304,44 +304,44 @@ static SolveGeom geom_for(int nbp_max, size_t esize, int PG, int RPT, size_t* sm
 template <typename T, int PG, int RPT>
 static void launch_cfg(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                        const T* fac, const cplx<T>* Pv, const cplx<T>* inva, cplx<T>* buf,
-                       int64_t rstride, int* err, cudaStream_t st) {
+                       int64_t rstride, DevStatus ds, cudaStream_t st) {
     size_t smem = 0;
     SolveGeom g = geom_for(nbp_max, sizeof(T), PG, RPT, &smem);
     cudaFuncSetAttribute(solve_kernel<T, PG, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     dim3 grid(ntask, (nrhs + PG - 1) / PG);
     solve_kernel<T, PG, RPT><<<grid, g.ncons + 32, smem, st>>>(tasks, subs, nrhs, fac, Pv, inva,
-                                                               buf, rstride, g, nbp_max, err);
+                                                               buf, rstride, g, nbp_max, ds);
 }
 
 template <typename T, int PG>
 static void launch_pg(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                       const T* fac, const cplx<T>* Pv, const cplx<T>* inva, cplx<T>* buf,
-                      int64_t rstride, int* err, cudaStream_t st) {
+                      int64_t rstride, DevStatus ds, cudaStream_t st) {
     if (nbp_max <= 960)
-        launch_cfg<T, PG, 1>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, err, st);
+        launch_cfg<T, PG, 1>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, ds, st);
     else
-        launch_cfg<T, PG, 2>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, err, st);
+        launch_cfg<T, PG, 2>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, ds, st);
 }
 
 template <typename T>
 void launch_solve(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                   int panel, const T* fac, const cplx<T>* Pv, const cplx<T>* inva, cplx<T>* buf,
-                  int64_t rstride, int* err, cudaStream_t st) {
+                  int64_t rstride, DevStatus ds, cudaStream_t st) {
     if (ntask == 0) return;
     switch (panel) {
-        case 1: launch_pg<T, 1>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, err, st); break;
-        case 2: launch_pg<T, 2>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, err, st); break;
-        case 4: launch_pg<T, 4>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, err, st); break;
-        default: launch_pg<T, 8>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, err, st); break;
+        case 1: launch_pg<T, 1>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, ds, st); break;
+        case 2: launch_pg<T, 2>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, ds, st); break;
+        case 4: launch_pg<T, 4>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, ds, st); break;
+        default: launch_pg<T, 8>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, ds, st); break;
     }
 }
 
 template void launch_solve<float>(const Task*, int, const SubDesc*, int, int, int, const float*,
                                   const cplx<float>*, const cplx<float>*, cplx<float>*, int64_t,
-                                  int*, cudaStream_t);
+                                  DevStatus, cudaStream_t);
 template void launch_solve<double>(const Task*, int, const SubDesc*, int, int, int,
                                    const double*, const cplx<double>*, const cplx<double>*,
-                                   cplx<double>*, int64_t, int*, cudaStream_t);
+                                   cplx<double>*, int64_t, DevStatus, cudaStream_t);
 
 }  // namespace helm

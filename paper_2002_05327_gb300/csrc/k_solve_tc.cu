@@ -90,7 +90,7 @@ __device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr uint32_t kWaitLimit = kDrainPolls;
 
 }  // namespace
 
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(1024) solve_tc_kernel(const Task* __restrict__
                                                         const cplx<float>* __restrict__ Pv,
                                                         const cplx<float>* __restrict__ inva,
                                                         cplx<float>* buf, int64_t rstride,
-                                                        TcGeom G, int nbp_max, int* err) {
+                                                        TcGeom G, int nbp_max, DevStatus ds) {
     constexpr int PG = 4 * NT;
     constexpr int BS = 8 * NT + (NT > 1 ? 8 : 0);  // floats per B row
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -147,8 +147,8 @@ __global__ void __launch_bounds__(1024) solve_tc_kernel(const Task* __restrict__
         int issued = 0;
         for (int i = 0; i < total; ++i) {
             const int s = i % NS;
-            if (i >= NS && !mbar_wait(&empty[s], (uint32_t)(((i / NS) - 1) & 1), kWaitLimit)) {
-                atomicExch(err, 2);
+            if (i >= NS && !mbar_wait(&empty[s], (uint32_t)(((i / NS) - 1) & 1), ds.polls)) {
+                atomicExch(ds.err, 2);
                 *abort_flag = 1;
             }
             if (*abort_flag) break;
@@ -243,8 +243,8 @@ __global__ void __launch_bounds__(1024) solve_tc_kernel(const Task* __restrict__
         const float* Bc = bmat + bb * bmat_elems;
         for (int k = 0; k < per_line; ++k, ++ci) {
             const int s = ci % NS;
-            if (!*abort_flag && !mbar_wait(&full[s], (uint32_t)((ci / NS) & 1), kWaitLimit)) {
-                atomicExch(err, 2);
+            if (!*abort_flag && !mbar_wait(&full[s], (uint32_t)((ci / NS) & 1), ds.polls)) {
+                atomicExch(ds.err, 2);
                 *abort_flag = 1;
             }
             const int q0 = k * cq;
@@ -329,7 +329,7 @@ static TcGeom tc_geom(int nbp_max, int kpad, int mtiles, int MTW, int NT, size_t
 template <int NT, int MTW>
 static void launch_tc(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                       const float* fac, const cplx<float>* Pv, const cplx<float>* inva,
-                      cplx<float>* buf, int64_t rstride, int* err, cudaStream_t st) {
+                      cplx<float>* buf, int64_t rstride, DevStatus ds, cudaStream_t st) {
     const int mtiles = (nbp_max + 15) / 16;
     const int kpad = ((nbp_max + 3) & ~3);
     size_t smem = 0;
@@ -339,18 +339,18 @@ static void launch_tc(const Task* tasks, int ntask, const SubDesc* subs, int nbp
     dim3 grid(ntask, (nrhs + 4 * NT - 1) / (4 * NT));
     solve_tc_kernel<NT, MTW><<<grid, 32 * G.ncw + 32, smem, st>>>(tasks, subs, nrhs, fac, Pv,
                                                                   inva, buf, rstride, G, nbp_max,
-                                                                  err);
+                                                                  ds);
 }
 
 void launch_solve_tc(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                      int panel, const float* fac, const cplx<float>* Pv, const cplx<float>* inva,
-                     cplx<float>* buf, int64_t rstride, int* err, cudaStream_t st) {
+                     cplx<float>* buf, int64_t rstride, DevStatus ds, cudaStream_t st) {
     if (ntask == 0) return;
     const int mtiles = (nbp_max + 15) / 16;
     const int MTW = mtiles <= 31 ? 1 : mtiles <= 62 ? 2 : 4;
     const bool wide = panel >= 8;
 #define HELM_TC(NT_, MTW_) \
-    launch_tc<NT_, MTW_>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, err, st)
+    launch_tc<NT_, MTW_>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, ds, st)
     if (MTW == 1) {
         if (panel >= 16) HELM_TC(4, 1); else if (wide) HELM_TC(2, 1); else HELM_TC(1, 1);
     } else if (MTW == 2) {

@@ -136,7 +136,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-constexpr uint32_t kWait = 1u << 22;
+constexpr uint32_t kWait = kDrainPolls;
 constexpr int kChunkK = 32;        // K values per 128-byte row
 constexpr int kTileBytes = 128 * 128;  // 128 rows x 128 B
 
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
     const Task* __restrict__ tasks, const SubDesc* __restrict__ subs, int nrhs, int CR,
     const float* __restrict__ afac, const int64_t* __restrict__ afac_off,
     const cplx<float>* __restrict__ Pv, const cplx<float>* __restrict__ inva, cplx<float>* buf,
-    int64_t rstride, int nstage, int* err) {
+    int64_t rstride, int nstage, DevStatus ds) {
     constexpr int kN = 2 * PG;              // real columns
     constexpr int kBChunkBytes = kN * 128;  // B rows of one K chunk
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -296,8 +296,8 @@ __global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
             int issued = 0;
             for (int i = 0; i < total_chunks; ++i) {
                 const int s = i % NS;
-                if (i >= NS && !mb_wait(empty(s), (uint32_t)(((i / NS) - 1) & 1), kWait)) {
-                    atomicExch(err, 2);
+                if (i >= NS && !mb_wait(empty(s), (uint32_t)(((i / NS) - 1) & 1), ds.polls)) {
+                    atomicExch(ds.err, 2);
                     *abort_flag = 1;
                 }
                 if (*abort_flag) break;
@@ -322,8 +322,8 @@ __global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
             constexpr uint32_t idesc = idesc_tf32(128, kN);
             const uint32_t dacc = tmem + (uint32_t)(q * kN);
             for (int step = 0; step < nsteps && !*abort_flag; ++step) {
-                if (!mb_wait_cluster(b_ready(step), (uint32_t)((step >> 1) & 1), kWait)) {
-                    atomicExch(err, 2);
+                if (!mb_wait_cluster(b_ready(step), (uint32_t)((step >> 1) & 1), ds.polls)) {
+                    atomicExch(ds.err, 2);
                     *abort_flag = 1;
                     break;
                 }
@@ -334,8 +334,8 @@ __global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
                 for (int kc = q; kc < nkc; kc += kIssuers) {
                     const int ci = step * nkc + kc;
                     const int s = ci % NS;
-                    if (!mb_wait(full(s), (uint32_t)((ci / NS) & 1), kWait)) {
-                        atomicExch(err, 2);
+                    if (!mb_wait(full(s), (uint32_t)((ci / NS) & 1), ds.polls)) {
+                        atomicExch(ds.err, 2);
                         *abort_flag = 1;
                         break;
                     }
@@ -428,9 +428,9 @@ __global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
             const bool fwd = step < nl;
             const int j = fwd ? step : 2 * nl - 2 - step;
             load_operand(step + 1, pre_next);
-            bool bad = *abort_flag || !mb_wait(acc_full, (uint32_t)(step & 1), kWait);
+            bool bad = *abort_flag || !mb_wait(acc_full, (uint32_t)(step & 1), ds.polls);
             if (__any_sync(0xffffffffu, bad)) {  // warp-uniform before the collective load
-                atomicExch(err, 2);
+                atomicExch(ds.err, 2);
                 *abort_flag = 1;
                 break;
             }
@@ -498,7 +498,7 @@ int64_t umma_factor_bytes(const SubDesc& S, int mt) { return umma_line_bytes(S.n
 template <int PG>
 static void launch_pg(const Task* tasks, int ntask, const SubDesc* subs, int CR, int nkc_max,
                       int nrhs, const float* afac, const int64_t* afac_off, const cplx<float>* Pv,
-                      const cplx<float>* inva, cplx<float>* buf, int64_t rstride, int* err,
+                      const cplx<float>* inva, cplx<float>* buf, int64_t rstride, DevStatus ds,
                       cudaStream_t st) {
     const size_t bbuf = (size_t)nkc_max * 2 * PG * 128;
     const size_t fixed = 2 * bbuf + 8 * 64 + 64 + 1024;  // B[2], barriers, slots, alignment
@@ -519,7 +519,7 @@ static void launch_pg(const Task* tasks, int ntask, const SubDesc* subs, int CR,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, solve_umma_kernel<PG>, tasks, subs, nrhs, CR, afac, afac_off, Pv, inva,
-                       buf, rstride, ns, err);
+                       buf, rstride, ns, ds);
 }
 
 bool umma_supported(int nblk_max) { return umma_tiles(nblk_max) <= 2; }
@@ -527,13 +527,13 @@ bool umma_supported(int nblk_max) { return umma_tiles(nblk_max) <= 2; }
 void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
                        int panel, const float* afac, const int64_t* afac_off,
                        const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf,
-                       int64_t rstride, int* err, cudaStream_t st) {
+                       int64_t rstride, DevStatus ds, cudaStream_t st) {
     if (ntask == 0) return;
     const int CR = umma_tiles(nblk_max);  // cluster of one CTA per 128-row tile
     int nkc = 0;
     umma_line_bytes(nblk_max, CR, &nkc);
 #define HELM_UMMA(PG_) \
-    launch_pg<PG_>(tasks, ntask, subs, CR, nkc, nrhs, afac, afac_off, Pv, inva, buf, rstride, err, st)
+    launch_pg<PG_>(tasks, ntask, subs, CR, nkc, nrhs, afac, afac_off, Pv, inva, buf, rstride, ds, st)
     if (panel >= 32) HELM_UMMA(32); else if (panel >= 16) HELM_UMMA(16); else HELM_UMMA(8);
 #undef HELM_UMMA
 }

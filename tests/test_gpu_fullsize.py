@@ -1,0 +1,184 @@
+"""Parity at the full sizes of the seismic-shaped workloads.
+
+The 1064^2 layered workload (8x8 subdomains, 64 point sources) runs in the
+launch configuration the benchmark times: all right-hand sides in one call,
+TF32 tensor-core subdomain solves, FP64 GMRES to a relative residual of 1e-8,
+on the caller's stream.  The oracle checks, one by one, the outputs it can
+afford:
+  * sampled right-hand sides against its global direct solve (1e-6 relative
+    L2, the accuracy the method promises after refinement);
+  * one right-hand side of the raw DDM (both precisions) against its own
+    Algorithm 3.1;
+and every right-hand side through a property that holds at any size: the true
+FP64 residual, computed with the oracle's operator.
+
+The 544^2 adjoint workload (32 sources, 256 receivers) checks the
+receiver-misfit gradient taken through torch autograd (forward helm_solve,
+backward helm_adjoint + helm_gradient) against the oracle's gradient from
+direct solves, and against central differences of the library's own loss
+along two directions of m.
+"""
+import dataclasses
+
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import workloads as W
+from oracle import adjoint as OA
+from oracle import ddm as OD
+from oracle import helmholtz as OH
+
+pytestmark = pytest.mark.gpu
+
+SAMPLE = [0, 37, 63]   # right-hand sides checked against the direct solve
+DDM_RHS = 5            # right-hand side checked against the oracle's Algorithm 3.1
+
+
+@pytest.fixture(scope="module")
+def H():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2002_05327_gb300 as H
+    from paper_2002_05327_gb300.build import build
+    build()
+    return H
+
+
+def rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.fixture(scope="module")
+def wl2():
+    return W.config(2)
+
+
+@pytest.fixture(scope="module")
+def oracle_ddm2(wl2):
+    """Algorithm 3.1 (oracle) applied to J f of one right-hand side."""
+    return OD.ddm_solution(dataclasses.replace(wl2, f=wl2.f[[DDM_RHS]]))[0]
+
+
+@pytest.fixture(scope="module")
+def gpu2(H, wl2):
+    import torch
+    stream = torch.cuda.current_stream().cuda_stream
+    ctx = H.helm_setup_workload(wl2, precision=H.HELM_PREC_TF32, stream=stream)
+    H.helm_factor(ctx)
+    F = torch.from_numpy(wl2.f).cuda()
+    U, st = H.helm_solve(ctx, F, rtol=1e-8, maxit=60)
+    Z = H.helm_apply_ddm(ctx, F)
+    out = (U.cpu().numpy(), Z[DDM_RHS].cpu().numpy(), st)
+    ctx.close()
+    return out
+
+
+def test_bench_workload_sampled_rhs_match_direct_solve(wl2, gpu2):
+    U, _, st = gpu2
+    ref = OH.solve_global(dataclasses.replace(wl2, f=wl2.f[SAMPLE]))
+    errs = [rel(U[s], ref[i]) for i, s in enumerate(SAMPLE)]
+    assert max(errs) <= 1e-6, (errs, st)
+
+
+def test_bench_workload_every_rhs_true_residual(wl2, gpu2):
+    """GMRES stops when its FP64 residual |Jf - Au|/|Jf| is <= 1e-8 for every
+    right-hand side; the oracle's own operator must see the same."""
+    U, _, _ = gpu2
+    A, J = OH.global_operator(wl2)
+    res = []
+    for s in range(wl2.nrhs):
+        b = J * wl2.f[s].ravel()
+        res.append(np.linalg.norm(b - A @ U[s].ravel()) / np.linalg.norm(b))
+    assert max(res) <= 1.5e-8, max(res)
+
+
+def test_bench_workload_raw_tf32_ddm_matches_algorithm(gpu2, oracle_ddm2):
+    """One DDM application of all 64 right-hand sides in one call; the sampled
+    one equals the oracle's Algorithm 3.1 within the TF32 tolerance."""
+    _, z, _ = gpu2
+    assert rel(z, oracle_ddm2) < 3e-2
+
+
+def test_bench_workload_raw_fp64_ddm_matches_algorithm(H, wl2, oracle_ddm2):
+    """The plain complex128 GPU DDM (the comparator the benchmark times) on all
+    64 right-hand sides at once."""
+    import torch
+    ctx = H.helm_setup_workload(wl2, precision=H.HELM_PREC_F64,
+                                stream=torch.cuda.current_stream().cuda_stream)
+    H.helm_factor(ctx)
+    Z = H.helm_apply_ddm(ctx, torch.from_numpy(wl2.f).cuda())
+    z = Z[DDM_RHS].cpu().numpy()
+    ctx.close()
+    assert rel(z, oracle_ddm2) < 1e-10
+
+
+# ----------------------------------------------------------------------------- adjoint
+def _spec(H, wl):
+    return dict(ndim=wl.ndim, n=wl.n, h=wl.h, omega=wl.omega, pml_width=wl.pml,
+                sigma0=wl.sigma0, nb=wl.nb, overlap=wl.overlap, power=wl.power, cuts=wl.cuts,
+                sub_pml=wl.sub_pml, precision=H.HELM_PREC_TF32)
+
+
+def test_adjoint_gradient_full_size(H):
+    """Config of the adjoint workload: 544^2 layered medium, 4x4 subdomains, 32
+    sources, 256 receivers; data d from the oracle's direct solve in the true
+    medium m_true; loss 1/2 sum |u(receivers) - d|^2 at the background m0."""
+    import torch
+    wl = W.config(5)
+    grid = wl.grid_shape
+    rec = wl.receivers
+    # oracle: direct solves with the global operator (one LU per medium)
+    A1, J1 = OH.global_operator(dataclasses.replace(wl, m=wl.meta["m_true"]))
+    lu1 = spla.splu(A1.tocsc(), permc_spec="COLAMD")
+    fJ = wl.f * J1.reshape(grid)[None]
+    d = OA.receiver_values(lu1.solve(np.ascontiguousarray(fJ.reshape(wl.nrhs, -1).T)).T
+                           .reshape(wl.f.shape), rec)
+    A0, J0 = OH.global_operator(wl)
+    lu0 = spla.splu(A0.tocsc(), permc_spec="COLAMD")
+
+    def solve0(B):
+        return lu0.solve(np.ascontiguousarray(B.reshape(B.shape[0], -1).T)).T.reshape(B.shape)
+
+    u0 = solve0(wl.f * J0.reshape(grid)[None])
+    lam = OA.adjoint_solve(solve0, OA.adjoint_source(u0, rec, d))
+    g_ref = OA.gradient(wl, u0, lam)
+    L_ref = OA.misfit(u0, rec, d)
+
+    # library, through torch autograd
+    spec = _spec(H, wl)
+    F = torch.from_numpy(wl.f).cuda()
+    dt = torch.from_numpy(d).cuda()
+    rx = torch.from_numpy(rec[:, 0]).cuda()
+    ry = torch.from_numpy(rec[:, 1]).cuda()
+
+    def loss(m, rtol):
+        U = H.HelmSolve.apply(m, F, spec, rtol, 100)
+        return 0.5 * (U[:, ry, rx] - dt).abs().pow(2).sum()
+
+    m = torch.tensor(wl.m, dtype=torch.float64, device="cuda", requires_grad=True)
+    L = loss(m, 1e-10)
+    L.backward()
+    g = m.grad.cpu().numpy()
+    assert abs(float(L.detach()) - L_ref) / L_ref < 1e-6
+    assert rel(g, g_ref) < 1e-6, rel(g, g_ref)
+
+    # central differences of the library's own loss along two directions v:
+    # the true perturbation m_true - m0 and a seeded smooth random field on
+    # the interior, each scaled so that eps * max|v| = 1e-5 max m (the
+    # truncation error is O(eps^2): with the oracle's direct solves the random
+    # direction gives 1.1e-4 at 1e-4 max m and 1.1e-6 at 1e-5 max m)
+    p = wl.pml
+    rng = np.random.default_rng(55)
+    from scipy.ndimage import gaussian_filter
+    v2 = np.zeros(grid)
+    v2[p:-p, p:-p] = gaussian_filter(rng.standard_normal((grid[0] - 2 * p, grid[1] - 2 * p)), 8.0)
+    with torch.no_grad():
+        for v in (wl.meta["m_true"] - wl.m, v2):
+            eps = 1e-5 * wl.m.max() / np.abs(v).max()
+            vt = torch.from_numpy(v).cuda()
+            m0 = torch.from_numpy(wl.m).cuda()
+            fd = (float(loss(m0 + eps * vt, 1e-12)) - float(loss(m0 - eps * vt, 1e-12))) / (2 * eps)
+            dd = float(np.sum(g * v))
+            assert abs(fd - dd) <= 1e-4 * abs(dd), (fd, dd)

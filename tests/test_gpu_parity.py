@@ -186,6 +186,36 @@ def test_errors_are_reported(H):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+def test_expired_wait_is_reported_and_context_stays_usable(H, prec):
+    """wait_limit=-1 makes every ordinary bounded wait inside the subdomain-solve
+    kernels give up at its first check, so each kernel takes its abort path:
+    raise the device error word, stop issuing work, drain the copies and MMAs
+    it started, free TMEM, exit.  Every entry point that runs a solve must
+    report HELM_ERR_TIMEOUT (the error word is cleared after each report), and
+    a fresh context on the same device must still give the right answer.
+    The wide case runs the tcgen05 kernel as 2-CTA clusters."""
+    wl = CASES["2d-wide-2x2"]()
+    bad = _ctx(H, wl, prec, wait_limit=-1)
+    for _ in range(2):
+        with pytest.raises(H.HelmError) as e:
+            H.helm_apply_ddm(bad, wl.f)
+        assert e.value.code == H.HELM_ERR_TIMEOUT
+    with pytest.raises(H.HelmError) as e:
+        H.helm_solve(bad, wl.f, rtol=1e-8, maxit=5)
+    assert e.value.code == H.HELM_ERR_TIMEOUT
+    lo, hi = H.helm_window_info(bad, 0)
+    shape = tuple(reversed([b - a for a, b in zip(lo, hi)]))
+    with pytest.raises(H.HelmError) as e:
+        H.helm_subdomain_solve(bad, 0, np.ones((1,) + shape, dtype=np.complex128))
+    assert e.value.code == H.HELM_ERR_TIMEOUT
+    bad.close()
+    good = _ctx(H, wl, prec)
+    u = H.helm_apply_ddm(good, wl.f)
+    assert rel(u, OD.ddm_solution(wl)) < TOL[prec]
+    good.close()
+
+
 def test_deterministic_and_device_pointers(H):
     import torch
     wl = W.small_2d(nx=60, ny=52, nbx=4, nby=3, nrhs=5)

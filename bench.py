@@ -38,7 +38,7 @@ METRIC = "RHS solves/sec at 1e-6 rel. L2 (mixed vs plain FP64 GPU DDM); %tensor/
 # DRAM bytes (read + write) per launch of the tcgen05 solve kernel, averaged over the 252
 # solve launches of one step of this workload, from one single-pass ncu capture
 # (profiles/launches_2d-layered-1064sq-64rhs.md).  Set to None when the kernel changes.
-SOLVE_TRAFFIC_BYTES_PER_LAUNCH = 809.8e6
+SOLVE_TRAFFIC_BYTES_PER_LAUNCH = None
 UNIT = "RHS/s"
 
 
@@ -338,13 +338,13 @@ def main():
         "gmres": {"iters": iters, "applications": apps, "max_rel_resid": res,
                   "factor_ms": factor_ms, "levels": stats[0]["levels"],
                   "subdomain_solves_per_application": stats[0]["solves"]},
-        "roofline": {"kernel": ("solve_tc_kernel" if args.prec == "tf32" else "solve_kernel")
+        "roofline": {"kernel": ("solve_umma_kernel" if args.prec == "tf32" else "solve_kernel")
                      + " (subdomain forward/backward block solves)",
                      "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,
                      "traffic": (SOLVE_TRAFFIC_BYTES_PER_LAUNCH
-                                 if args.prec == "tf32" and args.workload == 2 and not args.nrhs
-                                 else None),
+                                 if SOLVE_TRAFFIC_BYTES_PER_LAUNCH and args.prec == "tf32"
+                                 and args.workload == 2 and not args.nrhs else None),
                      "traffic_unit": "bytes per launch", "peak_source": peak_src,
                      "tflops_achieved": tflops,
                      "bytes_per_launch": sol["bytes"] / max(1, sol["launches"]),

@@ -133,7 +133,8 @@ struct helm_ctx {
     // factors
     void* ufac = nullptr;              // tcgen05 tile image of the factors (TF32)
     int64_t* ufac_off = nullptr;       // byte offset per subdomain
-    int umma_mt = 0;                   // 128-row tiles per block (0: tcgen05 not used)
+    int umma_mt = 0;                   // CTAs per block in the tcgen05 solve (0: not used)
+    int umma_nblk = 0;                 // largest block of the tcgen05 solve
     void* fac = nullptr;
     size_t fac_bytes = 0;
     bool factored = false;
@@ -727,7 +728,7 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
             }
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
             if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
-                launch_solve_umma(t, nt, c->subs_d, c->umma_mt * 128, nrhs, panel,
+                launch_solve_umma(t, nt, c->subs_d, c->umma_nblk, nrhs, panel,
                                   static_cast<const float*>(c->ufac), c->ufac_off, c->Pv32,
                                   c->inva32, buf, rs, DevStatus{c->err_d, c->wait_polls}, c->stream);
             else if (c->prec == HELM_PREC_TF32)
@@ -1034,6 +1035,7 @@ int helm_factor(helm_ctx* c) {
         for (const SubDesc& S : c->subs_h) nblk_max = std::max(nblk_max, S.nblk);
         if (c->cfg.tc_kernel == 0 && umma_supported(nblk_max)) {
             c->umma_mt = umma_tiles(nblk_max);
+            c->umma_nblk = nblk_max;
             std::vector<int64_t> off;
             int64_t tot = 0;
             for (const SubDesc& S : c->subs_h) {
@@ -1179,7 +1181,7 @@ int helm_subdomain_solve(helm_ctx* c, int s, int nrhs, const void* R, void* U, i
                              static_cast<const double*>(c->fac), c->Pv64, c->inva64,
                              static_cast<cplx<double>*>(wb), we, DevStatus{c->err_d, c->wait_polls}, c->stream);
     else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
-        launch_solve_umma(td, 1, c->subs_d, c->umma_mt * 128, nrhs, panel,
+        launch_solve_umma(td, 1, c->subs_d, c->umma_nblk, nrhs, panel,
                           static_cast<const float*>(c->ufac), c->ufac_off, c->Pv32, c->inva32,
                           static_cast<cplx<float>*>(wb), we, DevStatus{c->err_d, c->wait_polls}, c->stream);
     else if (c->prec == HELM_PREC_TF32)

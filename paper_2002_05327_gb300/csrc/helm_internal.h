@@ -177,7 +177,8 @@ void launch_solve_tc(const Task* tasks, int ntask, const SubDesc* subs, int nbp_
 void launch_round_tf32(float* x, int64_t count, cudaStream_t st);
 
 // tcgen05 (5th-generation tensor core) subdomain solve, k_solve_umma.cu.  The
-// factors are repacked into 128-byte-swizzled K-major tiles of 128 rows.
+// factors are repacked into 128-byte-swizzled K-major images, the block rows
+// split evenly over the umma_tiles(n) CTAs of a cluster.
 int umma_tiles(int nblk_max);
 bool umma_supported(int nblk_max);
 int64_t umma_factor_bytes(const SubDesc& S, int mt);

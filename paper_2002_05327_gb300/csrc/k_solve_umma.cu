@@ -12,24 +12,36 @@
 // Layouts (all K-major with the 128-byte swizzle: rows of 32 TF32 values, the
 // 16-byte chunk c of row r stored at chunk c ^ (r % 8), 8-row groups 1024 B apart):
 //   * A: the factors are repacked once (repack_umma_kernel) into the exact
-//     shared-memory image, [line][K chunk of 32][M tile of 128 rows][16 KB], so a
-//     whole K chunk of every M tile is one contiguous span for cp.async.bulk.
+//     shared-memory image, [line][K chunk of 32][CTA of the cluster][R rows x 128 B].
+//     The block rows are split evenly over the CR CTAs of a cluster (R = n/CR
+//     rounded up to 8 rows), so each K chunk of each CTA is one contiguous span
+//     for cp.async.bulk and a CTA streams only R*128 bytes per chunk: the ring
+//     then holds more than one line step, and the next step's operand arrives
+//     while the current one is multiplied.
 //   * B: built in shared memory by the epilogue threads, [K chunk][N rows][128 B].
 //
-// Roles (one CTA per (task, panel of PG right-hand sides, 128-row M tile);
-// the CTAs of the M tiles of a block form a thread-block cluster, N = 2 PG):
+// Roles (one CTA per (task, panel of PG right-hand sides, R-row slice of the
+// block); the CR slices of a block form a thread-block cluster, N = 2 PG;
+// each MMA has M = 128, and accumulator rows R..127 are ignored):
 //   warps 0-3   epilogue: thread = one block row p; reads its row of the
 //               accumulator from TMEM (tcgen05.ld), stores y or u, and writes
-//               row p of the next B into every CTA of the cluster (DSMEM)
-//   warp 4      producer: bulk copies of this CTA's A tile, chunk by chunk,
-//               into a ring deep enough to hold most of a line
-//   warp 5      TMEM allocation; lane 0 issues the MMAs and commits
+//               row p of the next B into its own CTA; one thread then pushes
+//               the CTA's rows of B to the peer CTA with one bulk copy (DSMEM)
+//   warps 4-7   producers: lane 0 of warp 4+q bulk-copies the K chunks at
+//               stream positions q, q+4, ... of this CTA's slice of A (own
+//               rows' chunks first) into sub-ring q of the ring
+//   warps 8-11  lane 0 of warp 8+q issues the MMAs of those chunks into its
+//               own accumulator and commits; warp 8 also allocates TMEM
 // Handshakes are mbarriers: full/empty per stage (TMA bytes / tcgen05.commit),
-// acc_full per step (tcgen05.commit), b_ready per step (the epilogue threads
-// of every CTA of the cluster, remote arrivals with release semantics).
+// acc_full per step (tcgen05.commit), b_local per step (own rows of B
+// written: the K chunks of this CTA's rows are multiplied at once) and
+// b_remote per step (the peer's rows have arrived: armed by this CTA with
+// the bytes it expects, completed by the peer's bulk copy), so the exchange
+// overlaps the MMAs of the CTA's own chunks.
 // Every wait is bounded; on expiry the CTA raises the device error word, each
 // role leaves its loop, outstanding copies and MMAs are drained (bounded),
-// and TMEM is freed before the CTA exits.
+// the two CTAs drain the bulk copies between them, and TMEM is freed before
+// the CTA exits.
 #include <algorithm>
 
 #include "helm_internal.h"
@@ -52,21 +64,6 @@ __device__ __forceinline__ bool mb_wait(uint32_t bar, uint32_t parity, uint32_t 
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-// Bounded wait with cluster-scope acquire: pairs with remote release arrivals.
-__device__ __forceinline__ bool mb_wait_cluster(uint32_t bar, uint32_t parity, uint32_t limit) {
-    uint32_t done = 0;
-    for (uint32_t it = 0; it < limit; ++it) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2;\n\t"
             "selp.u32 %0, 1, 0, p;\n\t}"
             : "=r"(done)
             : "r"(bar), "r"(parity)
@@ -123,17 +120,22 @@ __device__ __forceinline__ void tc_fence_before() {
 __device__ __forceinline__ void tc_fence_after() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
-    uint32_t r[16];
+// Issue a 32-lane x 16-column TMEM load without waiting for it; tmem_wait_ld
+// then waits for every load the thread has issued and ties the registers to
+// that wait, so no use of them can be scheduled before it.
+__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
     asm volatile(
         "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
         : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
           "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
           "=r"(r[14]), "=r"(r[15])
         : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void tmem_pin16(uint32_t (&r)[16]) {
+    asm volatile(""
+                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
+                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
+                   "+r"(r[13]), "+r"(r[14]), "+r"(r[15]));
 }
 
 constexpr uint32_t kWait = kDrainPolls;
@@ -142,37 +144,43 @@ constexpr int kTileBytes = 128 * 128;  // 128 rows x 128 B
 
 }  // namespace
 
-// Bytes of one line's repacked A for a block of n rows stored with MT M tiles
-// of 128 rows (every subdomain of a context uses the same MT):
-// ceil(2*roundup4(n)/32) K chunks x MT tiles x 16 KB.
-__host__ __device__ inline int64_t umma_line_bytes(int n, int MT, int* nkc) {
+// Block rows held by each of the CR CTAs of a cluster: an even split rounded
+// up to 16 rows (whole 8-row swizzle groups of A, and whole 32-value K chunks
+// of B: 2 values per row), at most 128 = the MMA's M when n <= 128 CR.
+__host__ __device__ inline int umma_rows(int n, int CR) { return (((n + CR - 1) / CR) + 15) & ~15; }
+
+// Bytes of one line's repacked A for a block of n rows split over CR CTAs
+// (every subdomain of a context uses the same CR):
+// ceil(2*roundup4(n)/32) K chunks x CR slices x R rows x 128 B.
+__host__ __device__ inline int64_t umma_line_bytes(int n, int CR, int* nkc) {
     const int n4 = (n + 3) & ~3;
     const int kc = (2 * n4 + kChunkK - 1) / kChunkK;
     if (nkc) *nkc = kc;
-    return (int64_t)kc * MT * kTileBytes;
+    return (int64_t)kc * CR * umma_rows(n, CR) * 128;
 }
 
 // Repack the column-major factors of every subdomain (k_factor.cu layout) into
 // the swizzled tile image, rounding to TF32.  One thread per output float.
 __global__ void repack_umma_kernel(const SubDesc* __restrict__ subs, const float* __restrict__ fac,
-                                   const int64_t* __restrict__ dst_off, float* dst, int sub, int mt) {
+                                   const int64_t* __restrict__ dst_off, float* dst, int sub, int cr) {
     const SubDesc& S = subs[sub];
     int nkc;
-    const int64_t lb = umma_line_bytes(S.nblk, mt, &nkc) / 4;  // floats per line
+    const int64_t lb = umma_line_bytes(S.nblk, cr, &nkc) / 4;  // floats per line
+    const int R = umma_rows(S.nblk, cr);
     const int64_t total = lb * S.nlines;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= total) return;
     const int j = (int)(i / lb);
     int64_t rem = i % lb;
-    const int kc = (int)(rem / (mt * 4096));
-    rem %= (mt * 4096);
-    const int tile = (int)(rem / 4096);
-    const int off = (int)(rem % 4096);  // float offset in the 16 KB tile image
-    const int r = off / 32;             // row in tile
-    const int pos = off % 32;           // float position within the 128-byte row
+    const int kc = (int)(rem / (cr * R * 32));
+    rem %= (cr * R * 32);
+    const int slice = (int)(rem / (R * 32));
+    const int off = (int)(rem % (R * 32));  // float offset in the slice image
+    const int r = off / 32;                 // row in the slice
+    const int pos = off % 32;               // float position within the 128-byte row
     const int chunk = (pos / 4) ^ (r % 8);
     const int kk = chunk * 4 + (pos % 4);  // logical K within the chunk
-    const int p = tile * 128 + r;
+    const int p = slice * R + r;
     const int k = kc * kChunkK + kk;
     const int q = k >> 1, part = k & 1;
     float v = 0.f;
@@ -193,30 +201,55 @@ __device__ __forceinline__ uint32_t map_peer(uint32_t saddr, uint32_t rank) {
     asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
     return r;
 }
-__device__ __forceinline__ void st_cluster_v2(uint32_t addr, float a, float b) {
-    asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(addr), "f"(a), "f"(b) : "memory");
+// Bulk copy of this CTA's shared memory into a peer CTA's, completing as
+// transaction bytes on the peer's mbarrier (addresses from mapa).
+__device__ __forceinline__ void bulk_s2peer(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar) {
+    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "r"(src), "r"(bytes), "r"(bar)
+                 : "memory");
 }
-__device__ __forceinline__ void mb_arrive_cluster(uint32_t addr) {
-    asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(addr) : "memory");
+// Barriers among the 128 epilogue threads only (named barriers 1 and 2; the
+// producer and issuer warps never take part).  epi_any also ORs a flag over
+// them, so that all four epilogue warps take the same abort decision.
+__device__ __forceinline__ void epi_sync() {
+    __syncwarp();
+    asm volatile("bar.sync 2, 128;" ::: "memory");
+}
+__device__ __forceinline__ bool epi_any(bool flag) {
+    uint32_t out;
+    __syncwarp();
+    asm volatile(
+        "{\n\t.reg .pred q, p;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.or.pred p, 1, 128, q;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(out)
+        : "r"((uint32_t)flag)
+        : "memory");
+    return out != 0;
 }
 __device__ __forceinline__ void cluster_sync() {
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// One CTA per (task, panel of PG right-hand sides, 128-row M tile); the CTAs
-// of the M tiles of one block form a cluster of CR (1 or 2).  Each CTA streams
-// and multiplies only its own tile of D_j, holds the whole K extent of B, and
-// its epilogue writes the B rows of its block rows into every CTA of the
-// cluster (distributed shared memory) and arrives on every CTA's b_ready.
+// One CTA per (task, panel of PG right-hand sides, R-row slice of the block);
+// the slices of one block form a cluster of CR (1 or 2).  Each CTA streams and
+// multiplies only its own rows of D_j, holds the whole K extent of B, and its
+// epilogue writes the B rows of its block rows into both CTAs of the cluster.
 // B is double-buffered: a peer may be one step ahead.
 constexpr int kIssuers = 4;  // MMA-issuing warps; K chunks are dealt round-robin to them
+// One bulk-copy producer warp per issuer: a thread issues one cp.async.bulk
+// every ~350 ns whatever its size, so a single producer of 12 KB chunks
+// supplies only ~35 GB/s to its SM, and four supply four times that.
+constexpr int kWarpEpi = 4, kWarpProd = kWarpEpi, kWarpIss = kWarpProd + kIssuers;
+constexpr int kThreads = 32 * (kWarpIss + kIssuers);
 
 template <int PG>
-__global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
+__global__ void __launch_bounds__(kThreads) solve_umma_kernel(
     const Task* __restrict__ tasks, const SubDesc* __restrict__ subs, int nrhs, int CR,
     const float* __restrict__ afac, const int64_t* __restrict__ afac_off,
     const cplx<float>* __restrict__ Pv, const cplx<float>* __restrict__ inva, cplx<float>* buf,
-    int64_t rstride, int nstage, DevStatus ds) {
+    int64_t rstride, int nstage, uint32_t ring_bytes, DevStatus ds) {
     constexpr int kN = 2 * PG;              // real columns
     constexpr int kBChunkBytes = kN * 128;  // B rows of one K chunk
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -226,53 +259,88 @@ __global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
     const int n = S.nblk, nl = S.nlines;
     int nkc;
     const int64_t line_bytes = umma_line_bytes(n, CR, &nkc);
+    const int R = umma_rows(n, CR);                  // block rows of this CTA
+    const uint32_t stage_bytes = (uint32_t)R * 128;  // one K chunk of them
     const int NS = nstage;
     const uint32_t bbuf_bytes = (uint32_t)(nkc * kBChunkBytes);
 
-    // shared layout (1024-aligned): stages | B[2] | barriers | tmem slot | flag
+    // shared layout (1024-aligned): ring | B[2] | barriers | tmem slot | flag.
+    // The ring holds NS stages of stage_bytes plus a tail, ring_bytes in all
+    // (>= NS*stage_bytes + 16 KB - stage_bytes), so the 128-row operand an MMA
+    // reads from the last stage stays inside the ring; rows R..127 of a stage
+    // are whatever follows it and only feed accumulator rows that are ignored.
     const uint32_t base = (su32(smem_raw) + 1023u) & ~1023u;
     unsigned char* gbase = smem_raw + (base - su32(smem_raw));
     const uint32_t stage0 = base;
-    const uint32_t b0 = stage0 + NS * kTileBytes;
-    float* bgen = reinterpret_cast<float*>(gbase + NS * kTileBytes);
+    const uint32_t b0 = stage0 + ring_bytes;
+    float* bgen = reinterpret_cast<float*>(gbase + ring_bytes);
     const uint32_t bars = b0 + 2 * bbuf_bytes;
-    uint64_t* bars_g = reinterpret_cast<uint64_t*>(gbase + NS * kTileBytes + 2 * bbuf_bytes);
+    uint64_t* bars_g = reinterpret_cast<uint64_t*>(gbase + ring_bytes + 2 * bbuf_bytes);
+    // The ring is split into kIssuers sub-rings of NQ stages, one per issuer
+    // (stage q*NQ + k): the chunk at stream position li of a line goes to
+    // issuer li % kIssuers, which consumes its chunks in stream order, so every
+    // stage has one producer and one consumer in order and a parity wait on it
+    // always refers to the expected phase, however the copies complete.
+    const int NQ = NS / kIssuers;
     auto full = [&](int s) { return bars + 8u * s; };
     auto empty = [&](int s) { return bars + 8u * (NS + s); };
     const uint32_t acc_full = bars + 8u * (2 * NS);
-    // b_ready of step s is barrier s & 1: arrivals of consecutive steps never
-    // share a phase (a count-based phase cannot tell the steps apart, and a
-    // peer CTA may arrive for step s+1 before this CTA's last step-s arrival)
-    auto b_ready = [&](int step) { return bars + 8u * (2 * NS + 1 + (step & 1)); };
-    const uint32_t drain = bars + 8u * (2 * NS + 3);
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars_g + 2 * NS + 4);
+    // B of step s is double-buffered (buffer s & 1) and announced by two
+    // barriers of parity s & 1: b_local when this CTA's own rows are written
+    // (their K chunks can be multiplied at once), b_remote when every peer's
+    // rows have arrived.  Consecutive steps never share a phase (a peer may
+    // announce step s+1 before this CTA has consumed step s).
+    auto b_local = [&](int step) { return bars + 8u * (2 * NS + 1 + (step & 1)); };
+    auto b_remote = [&](int step) { return bars + 8u * (2 * NS + 3 + (step & 1)); };
+    const uint32_t drain = bars + 8u * (2 * NS + 5);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars_g + 2 * NS + 6);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    int* rem_done = reinterpret_cast<int*>(tmem_slot + 2);  // steps whose b_remote phase an issuer passed
+    volatile int* cnt_in = reinterpret_cast<volatile int*>(tmem_slot + 3);  // copies the peer sent (exit)
+    volatile int* cnt_out = reinterpret_cast<volatile int*>(tmem_slot + 4);  // copies this CTA sent
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nsteps = 2 * nl - 1;
-    const int total_chunks = nsteps * nkc;
+    // K chunks in the order this CTA streams and multiplies them: first the
+    // nloc chunks of its own block rows (B rows 2p, 2p+1 of rows p it owns),
+    // then the peers' chunks, which wait for the exchange
+    const int nkr = R / 16;  // K chunks per CTA's rows
+    int nloc = nkc - (int)rank * nkr;
+    nloc = nloc < 0 ? 0 : (nloc > nkr ? nkr : nloc);
+    auto chunk_at = [&](int li) { return (li + (int)rank * nkr) % nkc; };
+    // bytes of B rows this CTA sends to / receives from the peer per step
+    const uint32_t peer = rank ^ 1u;  // the other CTA of a 2-CTA cluster
+    int nloc_peer = nkc - (int)peer * nkr;
+    nloc_peer = nloc_peer < 0 ? 0 : (nloc_peer > nkr ? nkr : nloc_peer);
+    const uint32_t own_bytes = (uint32_t)nloc * kBChunkBytes;
+    const uint32_t peer_bytes = (uint32_t)nloc_peer * kBChunkBytes;
     // one accumulator of kN columns per issuer
     constexpr uint32_t kCols = kIssuers * kN <= 32 ? 32 : kIssuers * kN <= 64 ? 64 :
                                kIssuers * kN <= 128 ? 128 : 256;
 
     if (tid == 0) {
         *abort_flag = 0;
+        *rem_done = 0;
+        *cnt_in = 0;
+        *cnt_out = 0;
         for (int s = 0; s < NS; ++s) {
             mb_init(full(s), 1);
             mb_init(empty(s), 1);
         }
         mb_init(acc_full, kIssuers);
-        mb_init(b_ready(0), 128 * CR);  // every epilogue thread of every CTA of the cluster
-        mb_init(b_ready(1), 128 * CR);
+        mb_init(b_local(0), 1);  // this CTA's epilogue
+        mb_init(b_local(1), 1);
+        mb_init(b_remote(0), 1);  // this CTA's epilogue arms it for the peer's rows (unused if CR = 1)
+        mb_init(b_remote(1), 1);
         mb_init(drain, kIssuers);  // completes once every issuer's MMAs have
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     for (uint32_t i = tid; i < 2 * bbuf_bytes / 4; i += blockDim.x) bgen[i] = 0.f;
     {
         float* sg = reinterpret_cast<float*>(gbase);
-        for (uint32_t i = tid; i < (uint32_t)NS * kTileBytes / 4; i += blockDim.x) sg[i] = 0.f;
+        for (uint32_t i = tid; i < ring_bytes / 4; i += blockDim.x) sg[i] = 0.f;
     }
-    if (warp == 5) {
+    if (warp == kWarpIss) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                          su32(tmem_slot)),
                      "r"(kCols)
@@ -285,44 +353,46 @@ __global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    if (warp == 4) {
-        // ====================================================== producer
+    if (warp >= kWarpProd && warp < kWarpProd + kIssuers) {
+        // ====================================================== producers
+        // producer p fills sub-ring p with the chunks at stream positions
+        // p, p + kIssuers, ... of every line, in order
+        const int pq = warp - kWarpProd;
         if (lane == 0) {
             const char* abase = reinterpret_cast<const char*>(afac) + afac_off[tk.sub];
-            int rows = n - (int)rank * 128;
-            rows = rows < 8 ? 8 : ((rows + 7) & ~7);
-            if (rows > 128) rows = 128;
-            const uint32_t copy_bytes = (uint32_t)(rows * 128);
-            int issued = 0;
-            for (int i = 0; i < total_chunks; ++i) {
-                const int s = i % NS;
-                if (i >= NS && !mb_wait(empty(s), (uint32_t)(((i / NS) - 1) & 1), ds.polls)) {
-                    atomicExch(ds.err, 2);
-                    *abort_flag = 1;
-                }
-                if (*abort_flag) break;
-                const int step = i / nkc, kc = i % nkc;
+            int k = 0;  // chunks put into this sub-ring so far
+            for (int step = 0; step < nsteps && !*abort_flag; ++step) {
                 const int j = step < nl ? step : 2 * nl - 2 - step;
-                mb_expect_tx(full(s), copy_bytes);
-                bulk_g2s(stage0 + s * kTileBytes,
-                         abase + (int64_t)j * line_bytes + ((int64_t)kc * CR + rank) * kTileBytes,
-                         copy_bytes, full(s));
-                issued = i + 1;
+                for (int li = pq; li < nkc; li += kIssuers) {
+                    const int s = pq * NQ + k % NQ;
+                    if (k >= NQ && !mb_wait(empty(s), (uint32_t)(((k / NQ) - 1) & 1), ds.polls)) {
+                        atomicExch(ds.err, 2);
+                        *abort_flag = 1;
+                    }
+                    if (*abort_flag) break;
+                    const int64_t chunk_off = ((int64_t)chunk_at(li) * CR + rank) * stage_bytes;
+                    mb_expect_tx(full(s), stage_bytes);
+                    bulk_g2s(stage0 + s * stage_bytes, abase + (int64_t)j * line_bytes + chunk_off, stage_bytes,
+                             full(s));
+                    ++k;
+                }
             }
-            for (int i = (issued > NS ? issued - NS : 0); i < issued; ++i)
-                mb_wait(full(i % NS), (uint32_t)((i / NS) & 1), kWait);
+            // drain: every issued copy lands before the shared memory is released
+            for (int kk = (k > NQ ? k - NQ : 0); kk < k; ++kk)
+                mb_wait(full(pq * NQ + kk % NQ), (uint32_t)((kk / NQ) & 1), kWait);
         }
-    } else if (warp >= 5 && warp < 5 + kIssuers) {
+    } else if (warp >= kWarpIss && warp < kWarpIss + kIssuers) {
         // ====================================================== MMA issuers
-        // issuer q takes the K chunks kc = q, q + kIssuers, ... of every line
-        // into its own accumulator (columns q*kN ...), so the per-instruction
-        // issue latency of the chunks overlaps across warps
-        const int q = warp - 5;
+        // issuer q takes the chunks at positions q, q + kIssuers, ... of the
+        // stream order of every line into its own accumulator (columns q*kN
+        // ...), so the per-instruction issue latency overlaps across warps
+        const int q = warp - kWarpIss;
         if (lane == 0) {
             constexpr uint32_t idesc = idesc_tf32(128, kN);
             const uint32_t dacc = tmem + (uint32_t)(q * kN);
+            int k = 0;  // chunks of this issuer so far (its sub-ring sequence)
             for (int step = 0; step < nsteps && !*abort_flag; ++step) {
-                if (!mb_wait_cluster(b_ready(step), (uint32_t)((step >> 1) & 1), ds.polls)) {
+                if (!mb_wait(b_local(step), (uint32_t)((step >> 1) & 1), ds.polls)) {
                     atomicExch(ds.err, 2);
                     *abort_flag = 1;
                     break;
@@ -330,17 +400,29 @@ __global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
                 tc_fence_after();
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 const uint64_t bdesc0 = desc_sw128(b0 + (step & 1) * bbuf_bytes);
-                bool first = true;
-                for (int kc = q; kc < nkc; kc += kIssuers) {
-                    const int ci = step * nkc + kc;
-                    const int s = ci % NS;
-                    if (!mb_wait(full(s), (uint32_t)((ci / NS) & 1), ds.polls)) {
+                bool first = true, peers_in = CR == 1;
+                for (int li = q; li < nkc; li += kIssuers) {
+                    if (li >= nloc && !peers_in) {
+                        if (!mb_wait(b_remote(step), (uint32_t)((step >> 1) & 1), ds.polls)) {
+                            atomicExch(ds.err, 2);
+                            *abort_flag = 1;
+                            break;
+                        }
+                        tc_fence_after();
+                        peers_in = true;
+                        atomicMax(rem_done, step + 1);
+                    }
+                    const int kc = chunk_at(li);
+                    const int s = q * NQ + k % NQ;
+                    const uint32_t par = (uint32_t)((k / NQ) & 1);
+                    ++k;
+                    if (!mb_wait(full(s), par, ds.polls)) {
                         atomicExch(ds.err, 2);
                         *abort_flag = 1;
                         break;
                     }
                     tc_fence_after();
-                    const uint64_t adesc = desc_sw128(stage0 + s * kTileBytes);
+                    const uint64_t adesc = desc_sw128(stage0 + s * stage_bytes);
                     const uint64_t bdesc = bdesc0 + (uint64_t)(kc * (kBChunkBytes >> 4));
 #pragma unroll
                     for (int kk = 0; kk < 4; ++kk)
@@ -351,7 +433,18 @@ __global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
                 }
                 if (*abort_flag) break;
                 // (an issuer without a chunk -- K shorter than kIssuers chunks -- commits
-                // nothing pending; the epilogue never reads its accumulator)
+                // nothing pending; the epilogue never reads its accumulator).  An
+                // issuer whose chunks are all local still waits for the peers' rows
+                // of this step before committing, so that b_remote's phases are
+                // consumed in step order by every issuer.
+                if (!peers_in) {
+                    if (!mb_wait(b_remote(step), (uint32_t)((step >> 1) & 1), ds.polls)) {
+                        atomicExch(ds.err, 2);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    atomicMax(rem_done, step + 1);
+                }
                 umma_commit(acc_full);
             }
             umma_commit(drain);
@@ -359,8 +452,10 @@ __global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
         }
     } else {
         // ====================================================== epilogue (warps 0-3)
-        const int p = (int)rank * 128 + warp * 32 + lane;  // owned block row
-        const bool rv = p < n;
+        const int lr = warp * 32 + lane;     // accumulator row (TMEM lane)
+        const int p = (int)rank * R + lr;    // block row, owned if lr < R
+        const bool own = lr < R;
+        const bool rv = own && p < n;
         const int n4 = (n + 3) & ~3;
         const cplx<float> pvp = rv ? Pv[S.coup_off + p] : mk<float>(0, 0);
         const cplx<float>* ia = inva + S.inva_off;
@@ -375,32 +470,53 @@ __global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
             const int chunk = (kkb / 4) ^ (row % 8);
             return (uint32_t)(kcb * kBChunkBytes + row * 128 + chunk * 16 + (kkb % 4) * 4);
         };
-        uint32_t peer_b[2] = {b0, b0}, peer_ready[2] = {b_ready(0), b_ready(0)};
+        const uint32_t peer_b = CR > 1 ? map_peer(b0, peer) : b0;
+        const uint32_t peer_remote = CR > 1 ? map_peer(b_remote(0), peer) : b_remote(0);  // parity 1: +8
+        // this CTA's rows of B: its nloc K chunks from chunk rank*nkr
+        const uint32_t own_off = (uint32_t)((int)rank * nkr) * kBChunkBytes;
+        const bool wr = own && p < n4;  // this thread writes B rows 2p, 2p+1
+        // B rows k0, k0+1 of right-hand side c: row 2c holds (Re r, -Im r),
+        // row 2c+1 holds (Im r, Re r); values rounded to TF32
+        auto put_local = [&](int bb, const cplx<float> (&v)[PG]) {
+            float* bl = reinterpret_cast<float*>(gbase + ring_bytes + (uint32_t)bb * bbuf_bytes);
 #pragma unroll
-        for (int r = 0; r < 2; ++r)
-            if (r < CR) {
-                peer_b[r] = map_peer(b0, (uint32_t)r);
-                peer_ready[r] = map_peer(b_ready(0), (uint32_t)r);  // b_ready(1) is 8 bytes on
+            for (int c = 0; c < PG; ++c) {
+                const float re = __uint_as_float(to_tf32(v[c].re)), im = __uint_as_float(to_tf32(v[c].im));
+                const float nim = __uint_as_float(to_tf32(-v[c].im));
+                *reinterpret_cast<float2*>(bl + boff(2 * c) / 4) = make_float2(re, nim);
+                *reinterpret_cast<float2*>(bl + boff(2 * c + 1) / 4) = make_float2(im, re);
             }
-        // write B rows k0, k0+1 for right-hand side c into buffer bb of every CTA
-        auto put_b = [&](int bb, int c, cplx<float> v) {
-            const float re = __uint_as_float(to_tf32(v.re)), im = __uint_as_float(to_tf32(v.im));
-            const float nim = __uint_as_float(to_tf32(-v.im));
-            const uint32_t o0 = (uint32_t)bb * bbuf_bytes + boff(2 * c);
-            const uint32_t o1 = (uint32_t)bb * bbuf_bytes + boff(2 * c + 1);
-#pragma unroll
-            for (int r = 0; r < 2; ++r)
-                if (r < CR) {
-                    st_cluster_v2(peer_b[r] + o0, re, nim);  // row 2c:   Re r, -Im r
-                    st_cluster_v2(peer_b[r] + o1, im, re);   // row 2c+1: Im r,  Re r
-                }
         };
-        auto signal = [&](int step) {  // B of `step` is written everywhere
-            asm volatile("fence.proxy.async.shared::cluster;" ::: "memory");
+        // Announce the B rows of `step`: each writer orders its stores before
+        // the async-proxy reads (tensor cores, bulk copy) and its TMEM loads
+        // before the thread sync; after the epilogue barrier one thread
+        //   * arrives on b_local: this CTA's own K chunks can be multiplied;
+        //   * (2-CTA clusters) arms b_remote for the peer's rows of this step
+        //     (one arrival + their bytes; they may land before or after), and
+        //     pushes this CTA's rows, one contiguous run of whole K chunks,
+        //     into the peer's B buffer with a bulk copy that completes on the
+        //     peer's b_remote.
+        // Buffer reuse is safe without further waits: the peer multiplies
+        // step s only after its own step s-1, which needed this CTA's rows of
+        // s-1, sent after this CTA finished multiplying s-2 -- and the same
+        // chain orders this CTA's next write of a buffer after the peer has
+        // received (and the copy has finished reading) its previous contents.
+        auto announce = [&](int step, const cplx<float> (&v)[PG]) {
+            if (wr) put_local(step & 1, v);
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tc_fence_before();
-#pragma unroll
-            for (int r = 0; r < 2; ++r)
-                if (r < CR) mb_arrive_cluster(peer_ready[r] + 8u * (step & 1));
+            epi_sync();
+            if (tid == 0) {
+                asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b_local(step)) : "memory");
+                if (CR > 1) {
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b_remote(step)),
+                                 "r"(peer_bytes)
+                                 : "memory");
+                    const uint32_t off = (uint32_t)(step & 1) * bbuf_bytes + own_off;
+                    if (own_bytes) bulk_s2peer(peer_b + off, b0 + off, own_bytes, peer_remote + 8u * (step & 1));
+                    *cnt_out = step + 1;  // steps armed and sent
+                }
+            }
         };
         // operand needed after the product of step s: b_{j+1} (forward line j)
         // or y_j (backward line j); loaded one whole step ahead
@@ -416,38 +532,50 @@ __global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
                 dst[c] = (rv && c < ncol && jj >= 0) ? V[(int64_t)(c0 + c) * rstride + (int64_t)jj * n + p]
                                                      : mk<float>(0, 0);
         };
-        cplx<float> pre[PG], pre_next[PG], outv[PG];
+        cplx<float> pre[PG], pre_next[PG], outv[PG], nbv[PG];
 #pragma unroll
-        for (int c = 0; c < PG; ++c) {
-            cplx<float> b = (rv && c < ncol) ? V[(int64_t)(c0 + c) * rstride + p] : mk<float>(0, 0);
-            if (p < n4) put_b(0, c, b);
-        }
+        for (int c = 0; c < PG; ++c)
+            nbv[c] = (rv && c < ncol) ? V[(int64_t)(c0 + c) * rstride + p] : mk<float>(0, 0);
         load_operand(0, pre);
-        signal(0);
+        announce(0, nbv);
         for (int step = 0; step < nsteps; ++step) {
             const bool fwd = step < nl;
             const int j = fwd ? step : 2 * nl - 2 - step;
             load_operand(step + 1, pre_next);
             bool bad = *abort_flag || !mb_wait(acc_full, (uint32_t)(step & 1), ds.polls);
-            if (__any_sync(0xffffffffu, bad)) {  // warp-uniform before the collective load
+            if (epi_any(bad)) {  // uniform over the epilogue: before the collective load and barriers
                 atomicExch(ds.err, 2);
                 *abort_flag = 1;
                 break;
             }
             tc_fence_after();
+            // sum of the issuers' partial accumulators (an issuer without a chunk --
+            // K shorter than kIssuers chunks -- holds none); loads go out in groups
+            // of at most 64 registers, each group waited for once
+            constexpr int kGroup = kN * kIssuers <= 64 ? kIssuers : (64 / kN > 0 ? 64 / kN : 1);
             float acc[kN];
 #pragma unroll
             for (int e = 0; e < kN; ++e) acc[e] = 0.f;
 #pragma unroll
-            for (int iq = 0; iq < kIssuers; ++iq) {
-                if (iq >= nkc) break;  // issuers without a chunk hold no partial sum
+            for (int g0 = 0; g0 < kIssuers; g0 += kGroup) {
+                uint32_t part[kGroup][kN / 16][16];
 #pragma unroll
-                for (int q = 0; q < kN / 16; ++q) {
-                    float part[16];
-                    tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16) + iq * kN + 16 * q, part);
+                for (int ig = 0; ig < kGroup; ++ig)
 #pragma unroll
-                    for (int e = 0; e < 16; ++e) acc[16 * q + e] += part[e];
-                }
+                    for (int q = 0; q < kN / 16; ++q)
+                        if (g0 + ig < nkc)
+                            tmem_ld16_async(tmem + ((uint32_t)(warp * 32) << 16) + (g0 + ig) * kN + 16 * q,
+                                            part[ig][q]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int ig = 0; ig < kGroup; ++ig)
+#pragma unroll
+                    for (int q = 0; q < kN / 16; ++q) {
+                        if (g0 + ig >= nkc) continue;
+                        tmem_pin16(part[ig][q]);
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) acc[16 * q + e] += __uint_as_float(part[ig][q][e]);
+                    }
             }
             cplx<float> coup = mk<float>(0, 0);
             if (rv) {
@@ -455,16 +583,14 @@ __global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
                 else if (fwd) coup = pvp * ia[nl - 1];            // c_{nl-2}
                 else if (j > 0) coup = pvp * ia[j];               // c_{j-1}
             }
-            const int nb = (step + 1) & 1;
 #pragma unroll
             for (int c = 0; c < PG; ++c) {
                 const cplx<float> y = mk<float>(acc[2 * c], acc[2 * c + 1]);
                 outv[c] = fwd ? y : pre[c] - y;
-                cplx<float> nbv = mk<float>(0, 0);
-                if (rv) nbv = (fwd && j + 1 < nl) ? pre[c] - coup * outv[c] : coup * outv[c];
-                if (step + 1 < nsteps && p < n4) put_b(nb, c, nbv);
+                nbv[c] = mk<float>(0, 0);
+                if (rv) nbv[c] = (fwd && j + 1 < nl) ? pre[c] - coup * outv[c] : coup * outv[c];
             }
-            if (step + 1 < nsteps) signal(step + 1);
+            if (step + 1 < nsteps) announce(step + 1, nbv);
             // global stores after the release-arrive, so it does not wait for them
 #pragma unroll
             for (int c = 0; c < PG; ++c) {
@@ -475,9 +601,37 @@ __global__ void __launch_bounds__(32 * (5 + kIssuers)) solve_umma_kernel(
     }
     tc_fence_before();
     __syncthreads();
-    if (CR > 1) cluster_sync();  // no CTA leaves while a peer may still write into it
+    if (CR > 1) {
+        // Drain the bulk copies between the two CTAs before either leaves (after
+        // an abort they may differ in how many steps they announced): each CTA
+        // learns how many copies its peer sent, arms the phases of b_remote it
+        // had not armed, and waits, in phase order, until every copy addressed
+        // to it has landed; the second cluster barrier then keeps each CTA
+        // resident until the copies reading its shared memory have finished.
+        if (tid == 0) {
+            const uint32_t dst = map_peer(su32((const void*)cnt_in), peer);
+            asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(dst), "r"((uint32_t)*cnt_out) : "memory");
+        }
+        __syncwarp();
+        cluster_sync();
+        if (tid == 0) {
+            const int k_in = *cnt_in, armed = *cnt_out;
+            for (int st = *reinterpret_cast<volatile int*>(rem_done); st < k_in; ++st) {
+                if (st >= armed)
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b_remote(st)),
+                                 "r"(peer_bytes)
+                                 : "memory");
+                if (!mb_wait(b_remote(st), (uint32_t)((st >> 1) & 1), kWait)) {
+                    atomicExch(ds.err, 2);
+                    break;
+                }
+            }
+        }
+        __syncwarp();
+        cluster_sync();
+    }
     tc_fence_after();
-    if (warp == 5)
+    if (warp == kWarpIss)
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols)
                      : "memory");
 }
@@ -495,20 +649,39 @@ int umma_tiles(int nblk_max) { return (nblk_max + 127) / 128; }
 
 int64_t umma_factor_bytes(const SubDesc& S, int mt) { return umma_line_bytes(S.nblk, mt, nullptr) * S.nlines; }
 
+// Shared-memory plan of a launch: ring of ns stages (kIssuers sub-rings, at
+// least 2 stages each, at most 32 stages) plus the 128-row tail of the last
+// stage, B[2], barriers and slots, alignment.  Returns the bytes, or 0 if the
+// minimum ring does not fit in a CTA's 227 KB.
+static size_t umma_smem_plan(int PG, int CR, int nblk_max, int* ns_out, uint32_t* ring_out) {
+    int nkc_max = 0;
+    umma_line_bytes(nblk_max, CR, &nkc_max);
+    const size_t sb_max = (size_t)umma_rows(nblk_max, CR) * 128;  // largest stage
+    const size_t bbuf = (size_t)nkc_max * 2 * PG * 128;
+    const size_t fixed = 2 * bbuf + 1024 + 1024;  // B[2]; barriers, slots; alignment
+    const size_t budget = 227 * 1024;
+    if (fixed + (2 * kIssuers - 1) * sb_max + kTileBytes > budget) return 0;
+    int ns = (int)((budget - fixed - kTileBytes) / sb_max) + 1;
+    if (ns > 32) ns = 32;  // barriers: 2 ns + 6 of 8 bytes within the 1 KB reserve
+    ns -= ns % kIssuers;
+    const uint32_t ring = (uint32_t)((ns - 1) * sb_max + kTileBytes);
+    *ns_out = ns;
+    *ring_out = ring;
+    return ring + fixed;
+}
+
 template <int PG>
-static void launch_pg(const Task* tasks, int ntask, const SubDesc* subs, int CR, int nkc_max,
+static void launch_pg(const Task* tasks, int ntask, const SubDesc* subs, int CR, int nblk_max,
                       int nrhs, const float* afac, const int64_t* afac_off, const cplx<float>* Pv,
                       const cplx<float>* inva, cplx<float>* buf, int64_t rstride, DevStatus ds,
                       cudaStream_t st) {
-    const size_t bbuf = (size_t)nkc_max * 2 * PG * 128;
-    const size_t fixed = 2 * bbuf + 8 * 64 + 64 + 1024;  // B[2], barriers, slots, alignment
-    int ns = (int)std::min<size_t>(16, (224 * 1024 - fixed) / kTileBytes);
-    if (ns < 2) ns = 2;
-    const size_t smem = ns * (size_t)kTileBytes + fixed;
+    int ns = 0;
+    uint32_t ring_bytes = 0;
+    const size_t smem = umma_smem_plan(PG, CR, nblk_max, &ns, &ring_bytes);
     cudaFuncSetAttribute(solve_umma_kernel<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ntask * CR, (nrhs + PG - 1) / PG, 1);
-    cfg.blockDim = dim3(32 * (5 + kIssuers), 1, 1);
+    cfg.blockDim = dim3(kThreads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -519,22 +692,29 @@ static void launch_pg(const Task* tasks, int ntask, const SubDesc* subs, int CR,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, solve_umma_kernel<PG>, tasks, subs, nrhs, CR, afac, afac_off, Pv, inva,
-                       buf, rstride, ns, ds);
+                       buf, rstride, ns, ring_bytes, ds);
 }
 
-bool umma_supported(int nblk_max) { return umma_tiles(nblk_max) <= 2; }
+bool umma_supported(int nblk_max) {
+    int ns;
+    uint32_t ring;
+    return umma_tiles(nblk_max) <= 2 && umma_smem_plan(8, umma_tiles(nblk_max), nblk_max, &ns, &ring) != 0;
+}
 
 void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
                        int panel, const float* afac, const int64_t* afac_off,
                        const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf,
                        int64_t rstride, DevStatus ds, cudaStream_t st) {
     if (ntask == 0) return;
-    const int CR = umma_tiles(nblk_max);  // cluster of one CTA per 128-row tile
-    int nkc = 0;
-    umma_line_bytes(nblk_max, CR, &nkc);
+    const int CR = umma_tiles(nblk_max);  // cluster of ceil(n / 128) CTAs, rows split evenly
+    int ns;
+    uint32_t ring;
+    // the widest panel (up to the one asked for) whose shared-memory plan fits
+    int pg = panel >= 32 ? 32 : panel >= 16 ? 16 : 8;
+    while (pg > 8 && umma_smem_plan(pg, CR, nblk_max, &ns, &ring) == 0) pg /= 2;
 #define HELM_UMMA(PG_) \
-    launch_pg<PG_>(tasks, ntask, subs, CR, nkc, nrhs, afac, afac_off, Pv, inva, buf, rstride, ds, st)
-    if (panel >= 32) HELM_UMMA(32); else if (panel >= 16) HELM_UMMA(16); else HELM_UMMA(8);
+    launch_pg<PG_>(tasks, ntask, subs, CR, nblk_max, nrhs, afac, afac_off, Pv, inva, buf, rstride, ds, st)
+    if (pg == 32) HELM_UMMA(32); else if (pg == 16) HELM_UMMA(16); else HELM_UMMA(8);
 #undef HELM_UMMA
 }
 

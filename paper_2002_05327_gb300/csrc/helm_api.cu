@@ -829,7 +829,7 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
     std::vector<cplx<double>> hd((size_t)(m + 2) * nrhs);
     std::vector<double> sc(nrhs);
     auto norms = [&](const cplx<double>* v, std::vector<double>& out) -> int {
-        { ProfScope ps_(c, HELM_K_KRYLOV, 2); launch_dots(v, 0, 1, v, Ng, nrhs, c->small_d, c->partial_d, nblk, c->stream); }
+        { ProfScope ps_(c, HELM_K_KRYLOV, 2); launch_norms2(v, Ng, nrhs, c->small_d, c->partial_d, nblk, c->stream); }
         CK(cudaMemcpyAsync(hd.data(), c->small_d, nrhs * 16, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
         for (int r = 0; r < nrhs; ++r) out[r] = std::sqrt(std::max(0.0, hd[r].re));

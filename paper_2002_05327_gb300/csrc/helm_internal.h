@@ -214,6 +214,8 @@ void launch_dots(const cplx<double>* V, int64_t vstride, int nv, const cplx<doub
 void launch_sub_combo(cplx<double>* w, const cplx<double>* V, int64_t vstride, int nv,
                       const cplx<double>* coef, int64_t n, int nrhs, double sign,
                       cudaStream_t st);  // w[c] += sign * sum_i coef[i*nrhs+c] V_i[c]
+void launch_norms2(const cplx<double>* v, int64_t n, int nrhs, cplx<double>* out,
+                   cplx<double>* partial, int nblk, cudaStream_t st);  // out[c] = |v[c]|^2
 // fused over nv vectors given as a device array of pointers (nv <= 64)
 void launch_mdots(const cplx<double>* const* V, int nv, const cplx<double>* w, int64_t n, int nrhs,
                   cplx<double>* out, cplx<double>* partial, int nblk, cudaStream_t st);

@@ -5,9 +5,76 @@
 //
 // Reductions are deterministic: every block reduces a fixed contiguous chunk
 // with a fixed tree, and a second pass sums the block partials in order.
+//
+// The Gram-Schmidt kernels (multi-vector dots, combinations, norms) keep their
+// vectors in FP64 but do their arithmetic in float-float ("double-float"
+// pairs hi + lo) on the FP32 pipes: on this GPU the FP64 pipe issues about
+// one sixty-fourth of the FP32 rate, and the FP64 versions of these kernels
+// ran at ~87% of it.  A double is split exactly into its top 24 and next 24
+// mantissa bits with integer operations only (conversions from double would
+// use the FP64 pipe); products are formed exactly with FMA (TwoProd) and sums
+// are compensated (TwoSum), so a dot or combination carries ~48 significant
+// bits -- ample for an Arnoldi relation to the 1e-8 residual the solver
+// targets.  Results go back to FP64 as hi + lo.
 #include "helm_internal.h"
 
 namespace helm {
+
+namespace {
+
+struct ff {
+    float hi, lo;
+};
+
+// x = hi + lo exactly up to the 5 lowest mantissa bits of x (48 of 53 bits
+// kept); values below 2^-126 (and the low part below 2^-75) read as 0, which
+// is far under anything these vectors hold.  Integer and FP32 operations only.
+__device__ __forceinline__ ff split_d(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
+    const int e = (int)((b >> 52) & 0x7FF);
+    const int ef = e - 1023 + 127;
+    if (e == 0x7FF) return {x != x ? __int_as_float(0x7FC00000) : __int_as_float((int)(sign | 0x7F800000u)), 0.f};
+    if (ef <= 0) return {0.f, 0.f};
+    if (ef >= 255) return {__int_as_float((int)(sign | 0x7F800000u)), 0.f};
+    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
+    const float hi = __uint_as_float(sign | ((unsigned int)ef << 23) | (unsigned int)(m >> 29));
+    const int es = e - 948;  // float exponent field of 2^(e - 1075), the weight of the low 29 bits
+    float lo = 0.f;
+    if (es > 0) lo = __uint2float_rn((unsigned int)(m & 0x1FFFFFFFull)) * __uint_as_float((unsigned int)es << 23);
+    return {hi, sign ? -lo : lo};
+}
+__device__ __forceinline__ double join_d(ff a) { return (double)a.hi + (double)a.lo; }
+
+// s += p with p's rounding error carried into the low word (Knuth's TwoSum)
+__device__ __forceinline__ void acc_add(ff& s, float p) {
+    const float t = s.hi + p;
+    const float v = t - s.hi;
+    const float e = (s.hi - (t - v)) + (p - v);
+    s.hi = t;
+    s.lo += e;
+}
+// s += a * b for a, b float-float: the head product exactly (TwoProd), the
+// cross terms and the tail into the low word
+__device__ __forceinline__ void acc_mul(ff& s, ff a, ff b) {
+    const float p = a.hi * b.hi;
+    const float e = fmaf(a.hi, b.hi, -p);
+    acc_add(s, p);
+    s.lo += fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+}
+__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
+// a + b of two accumulators (tree reductions)
+__device__ __forceinline__ ff ff_sum(ff a, ff b) {
+    ff s = a;
+    acc_add(s, b.hi);
+    s.lo += b.lo;
+    return s;
+}
+__device__ __forceinline__ ff shfl_down_ff(ff a, int o) {
+    return {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+}
+
+}  // namespace
 
 __device__ __forceinline__ void unflat(int64_t k, const int N[3], int g[3]) {
     g[0] = (int)(k % N[0]);
@@ -63,6 +130,26 @@ __global__ void apply_A_kernel(DevProblem P, Win<double> w, const double* __rest
             co[np++] = st.cm[a];
         }
         stride *= P.N[a];
+    }
+    // outside the PML every alpha is 1, so the coefficients are real (their
+    // imaginary parts are exact zeros) and each term needs two FMAs, not four
+    bool real = st.diag.im == 0.0;
+    for (int i = 0; i < np; ++i) real = real && co[i].im == 0.0;
+    if (real) {
+        for (int c = 0; c < nrhs; ++c) {
+            const cplx<double>* uc = u + (int64_t)c * Ng + k;
+            const cplx<double> u0 = uc[0];
+            double ar = st.diag.re * u0.re, ai = st.diag.re * u0.im;
+            for (int i = 0; i < np; ++i) {
+                const cplx<double> un = uc[off[i]];
+                ar = fma(co[i].re, un.re, ar);
+                ai = fma(co[i].re, un.im, ai);
+            }
+            cplx<double> out = mk<double>(-ar, -ai);
+            if (b) out = out + b[(int64_t)c * Ng + k];
+            r[(int64_t)c * Ng + k] = out;
+        }
+        return;
     }
     for (int c = 0; c < nrhs; ++c) {
         const cplx<double>* uc = u + (int64_t)c * Ng + k;
@@ -179,26 +266,32 @@ __global__ void conj_kernel(cplx<double>* v, int64_t count) {
 
 // ---- fused multi-vector kernels of classical Gram-Schmidt: one pass over w
 // and every V_i (V given as a device array of pointers)
-constexpr int kMaxV = 64;
 
 __global__ void mdots_partial_kernel(const cplx<double>* const* __restrict__ V, int nv,
                                      const cplx<double>* __restrict__ w, int64_t n, int nrhs,
                                      cplx<double>* partial, int nblk) {
-    __shared__ double sr[8][DOT_NT / 32], si[8][DOT_NT / 32];
+    __shared__ ff sr[8][DOT_NT / 32], si[8][DOT_NT / 32];
     const int blk = blockIdx.x, c = blockIdx.y, i0 = blockIdx.z * 8;
     const int nvb = min(8, nv - i0);
     const int64_t chunk = (n + nblk - 1) / nblk;
     const int64_t k0 = (int64_t)blk * chunk, k1 = min(n, k0 + chunk);
     const cplx<double>* wc = w + (int64_t)c * n;
-    double ar[8] = {0}, ai[8] = {0};
+    ff ar[8], ai[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) ar[i] = ai[i] = ff{0.f, 0.f};
     for (int64_t k = k0 + threadIdx.x; k < k1; k += DOT_NT) {
-        const cplx<double> b = wc[k];
+        const cplx<double> bw = wc[k];
+        const ff br = split_d(bw.re), bi = split_d(bw.im);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             if (i < nvb) {
-                const cplx<double> a = V[i0 + i][(int64_t)c * n + k];
-                ar[i] += a.re * b.re + a.im * b.im;
-                ai[i] += a.re * b.im - a.im * b.re;
+                const cplx<double> av = V[i0 + i][(int64_t)c * n + k];
+                const ff vr = split_d(av.re), vi = split_d(av.im);
+                // conj(v) w = (vr br + vi bi) + i (vr bi - vi br)
+                acc_mul(ar[i], vr, br);
+                acc_mul(ar[i], vi, bi);
+                acc_mul(ai[i], vr, bi);
+                acc_mul(ai[i], ff_neg(vi), br);
             }
         }
     }
@@ -206,8 +299,8 @@ __global__ void mdots_partial_kernel(const cplx<double>* const* __restrict__ V, 
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
         for (int o = 16; o > 0; o >>= 1) {
-            ar[i] += __shfl_down_sync(0xffffffffu, ar[i], o);
-            ai[i] += __shfl_down_sync(0xffffffffu, ai[i], o);
+            ar[i] = ff_sum(ar[i], shfl_down_ff(ar[i], o));
+            ai[i] = ff_sum(ai[i], shfl_down_ff(ai[i], o));
         }
         if (lane == 0) {
             sr[i][wp] = ar[i];
@@ -217,13 +310,46 @@ __global__ void mdots_partial_kernel(const cplx<double>* const* __restrict__ V, 
     __syncthreads();
     if (threadIdx.x < nvb) {
         const int i = threadIdx.x;
-        double r = 0, im = 0;
+        ff r = {0.f, 0.f}, im = {0.f, 0.f};
         for (int q = 0; q < DOT_NT / 32; ++q) {
-            r += sr[i][q];
-            im += si[i][q];
+            r = ff_sum(r, sr[i][q]);
+            im = ff_sum(im, si[i][q]);
         }
-        partial[((int64_t)(i0 + i) * nrhs + c) * nblk + blk] = mk<double>(r, im);
+        partial[((int64_t)(i0 + i) * nrhs + c) * nblk + blk] = mk<double>(join_d(r), join_d(im));
     }
+}
+
+// squared norms |v[c]|^2 into out[c] (imaginary part 0), float-float
+__global__ void norms_partial_kernel(const cplx<double>* __restrict__ v, int64_t n,
+                                     cplx<double>* partial, int nblk) {
+    __shared__ ff sr[DOT_NT / 32];
+    const int blk = blockIdx.x, c = blockIdx.y;
+    const int64_t chunk = (n + nblk - 1) / nblk;
+    const int64_t k0 = (int64_t)blk * chunk, k1 = min(n, k0 + chunk);
+    const cplx<double>* vc = v + (int64_t)c * n;
+    ff a = {0.f, 0.f};
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += DOT_NT) {
+        const cplx<double> x = vc[k];
+        const ff xr = split_d(x.re), xi = split_d(x.im);
+        acc_mul(a, xr, xr);
+        acc_mul(a, xi, xi);
+    }
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) a = ff_sum(a, shfl_down_ff(a, o));
+    if (lane == 0) sr[wp] = a;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        ff r = {0.f, 0.f};
+        for (int q = 0; q < DOT_NT / 32; ++q) r = ff_sum(r, sr[q]);
+        partial[(int64_t)c * nblk + blk] = mk<double>(join_d(r), 0.0);
+    }
+}
+
+void launch_norms2(const cplx<double>* v, int64_t n, int nrhs, cplx<double>* out,
+                   cplx<double>* partial, int nblk, cudaStream_t st) {
+    dim3 grid(nblk, nrhs);
+    norms_partial_kernel<<<grid, DOT_NT, 0, st>>>(v, n, partial, nblk);
+    dots_final_kernel<<<(nrhs + 127) / 128, 128, 0, st>>>(partial, nblk, nrhs, out);
 }
 
 void launch_mdots(const cplx<double>* const* V, int nv, const cplx<double>* w, int64_t n, int nrhs,
@@ -234,16 +360,30 @@ void launch_mdots(const cplx<double>* const* V, int nv, const cplx<double>* w, i
     dots_final_kernel<<<(count + 127) / 128, 128, 0, st>>>(partial, nblk, count, out);
 }
 
-// w[c] += sign * sum_i coef[i*nrhs+c] V_i[c]
+// w[c] += sign * sum_i coef[i*nrhs+c] V_i[c], accumulated in float-float
 __global__ void mcombo_kernel(cplx<double>* w, const cplx<double>* const* __restrict__ V, int nv,
                               const cplx<double>* __restrict__ coef, int64_t n, int nrhs,
                               double sign) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
     if (k >= n) return;
-    cplx<double> acc = w[(int64_t)c * n + k];
-    for (int i = 0; i < nv; ++i) acc = acc + sign * (coef[i * nrhs + c] * V[i][(int64_t)c * n + k]);
-    w[(int64_t)c * n + k] = acc;
+    const cplx<double> w0 = w[(int64_t)c * n + k];
+    ff ar = split_d(w0.re), ai = split_d(w0.im);
+    const float sg = sign < 0 ? -1.f : 1.f;  // sign is +-1
+    for (int i = 0; i < nv; ++i) {
+        const cplx<double> a = coef[i * nrhs + c];
+        ff cr = split_d(a.re), ci = split_d(a.im);
+        cr = {sg * cr.hi, sg * cr.lo};
+        ci = {sg * ci.hi, sg * ci.lo};
+        const cplx<double> v = V[i][(int64_t)c * n + k];
+        const ff vr = split_d(v.re), vi = split_d(v.im);
+        // (cr + i ci)(vr + i vi)
+        acc_mul(ar, cr, vr);
+        acc_mul(ar, ff_neg(ci), vi);
+        acc_mul(ai, cr, vi);
+        acc_mul(ai, ci, vr);
+    }
+    w[(int64_t)c * n + k] = mk<double>(join_d(ar), join_d(ai));
 }
 
 void launch_mcombo(cplx<double>* w, const cplx<double>* const* V, int nv, const cplx<double>* coef,

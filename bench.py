@@ -38,7 +38,7 @@ METRIC = "RHS solves/sec at 1e-6 rel. L2 (mixed vs plain FP64 GPU DDM); %tensor/
 # DRAM bytes (read + write) per launch of the tcgen05 solve kernel, averaged over the 252
 # solve launches of one step of this workload, from one single-pass ncu capture
 # (profiles/launches_2d-layered-1064sq-64rhs.md).  Set to None when the kernel changes.
-SOLVE_TRAFFIC_BYTES_PER_LAUNCH = None
+SOLVE_TRAFFIC_BYTES_PER_LAUNCH = 833.8e6
 UNIT = "RHS/s"
 
 

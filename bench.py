@@ -38,7 +38,7 @@ METRIC = "RHS solves/sec at 1e-6 rel. L2 (mixed vs plain FP64 GPU DDM); %tensor/
 # DRAM bytes (read + write) per launch of the tcgen05 solve kernel, averaged over the 252
 # solve launches of one step of this workload, from one single-pass ncu capture
 # (profiles/launches_2d-layered-1064sq-64rhs.md).  Set to None when the kernel changes.
-SOLVE_TRAFFIC_BYTES_PER_LAUNCH = 833.8e6
+SOLVE_TRAFFIC_BYTES_PER_LAUNCH = None
 UNIT = "RHS/s"
 
 
@@ -338,7 +338,7 @@ def main():
         "gmres": {"iters": iters, "applications": apps, "max_rel_resid": res,
                   "factor_ms": factor_ms, "levels": stats[0]["levels"],
                   "subdomain_solves_per_application": stats[0]["solves"]},
-        "roofline": {"kernel": ("solve_umma_kernel" if args.prec == "tf32" else "solve_kernel")
+        "roofline": {"kernel": ("solve_twist_kernel" if args.prec == "tf32" else "solve_kernel")
                      + " (subdomain forward/backward block solves)",
                      "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,

@@ -102,8 +102,10 @@ typedef struct {
     int32_t verbose;    /* 1: per-iteration residuals on stderr */
     void *stream;       /* cudaStream_t to run on; NULL = the library's own stream */
     int32_t profile;    /* 1: time every kernel launch with CUDA events (helm_profile_get) */
-    int32_t tc_kernel;  /* HELM_PREC_TF32 only: 0 = tcgen05/TMEM kernel where blocks have at
-                           most 256 rows, else mma.sync; 1 = always mma.sync */
+    int32_t tc_kernel;  /* HELM_PREC_TF32 only: 0 = tcgen05/TMEM kernels where blocks have at
+                           most 256 rows (the two-ended "twisted" form when every subdomain
+                           has at least 4 lines), else mma.sync; 1 = always mma.sync;
+                           2 = tcgen05, one-ended form only */
     int32_t wait_limit; /* bound of every ordinary spin-wait inside the subdomain-solve
                            kernels (a bulk copy, an MMA commit, a peer CTA's handshake),
                            in polls of the mbarrier: 0 = default (2^22 polls); n > 0 = n polls; -1 = no poll, so the first such wait

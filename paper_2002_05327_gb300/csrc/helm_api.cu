@@ -135,6 +135,7 @@ struct helm_ctx {
     int64_t* ufac_off = nullptr;       // byte offset per subdomain
     int umma_mt = 0;                   // CTAs per block in the tcgen05 solve (0: not used)
     int umma_nblk = 0;                 // largest block of the tcgen05 solve
+    bool umma_twist = false;           // tcgen05 solve in its twisted (two-ended) form
     void* fac = nullptr;
     size_t fac_bytes = 0;
     bool factored = false;
@@ -727,7 +728,11 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
                                      c->max_lines12, c->stream);
             }
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
-            if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
+            if (c->prec == HELM_PREC_TF32 && c->umma_twist)
+                launch_solve_twist(t, nt, c->subs_d, c->umma_nblk, nrhs, static_cast<const float*>(c->ufac),
+                                   c->ufac_off, c->Pv32, c->inva32, buf, rs,
+                                   DevStatus{c->err_d, c->wait_polls}, c->stream);
+            else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
                 launch_solve_umma(t, nt, c->subs_d, c->umma_nblk, nrhs, panel,
                                   static_cast<const float*>(c->ufac), c->ufac_off, c->Pv32,
                                   c->inva32, buf, rs, DevStatus{c->err_d, c->wait_polls}, c->stream);
@@ -1029,12 +1034,26 @@ int helm_factor(helm_ctx* c) {
         launch_factor_f32(c->subs_d, c->P.nsub, c->nbp_max, c->P, c->m32, c->an32, c->af32,
                           static_cast<float*>(c->fac), c->err_d, c->stream);
     if (c->prec == HELM_PREC_TF32) {
+        int nblk_max = 0, nl_min = 1 << 30;
+        for (const SubDesc& S : c->subs_h) {
+            nblk_max = std::max(nblk_max, S.nblk);
+            nl_min = std::min(nl_min, S.nlines);
+        }
+        const bool umma = c->cfg.tc_kernel != 1 && umma_supported(nblk_max);
+        const bool twist = umma && c->cfg.tc_kernel != 2 && twist_supported(nblk_max, nl_min);
+        float* fac2 = nullptr;
+        if (twist) {
+            // the far half of every subdomain's lines, eliminated from the far end
+            // (before the standard factors are rounded: the middle block uses one)
+            CK(cudaMalloc(&fac2, c->fac_bytes));
+            launch_factor_twist_f32(c->subs_d, c->P.nsub, c->nbp_max, c->P, c->m32, c->an32, c->af32,
+                                    static_cast<const float*>(c->fac), fac2, c->err_d, c->stream);
+        }
         launch_round_tf32(static_cast<float*>(c->fac), (int64_t)(c->fac_bytes / sizeof(float)),
                           c->stream);
-        int nblk_max = 0;
-        for (const SubDesc& S : c->subs_h) nblk_max = std::max(nblk_max, S.nblk);
-        if (c->cfg.tc_kernel == 0 && umma_supported(nblk_max)) {
-            c->umma_mt = umma_tiles(nblk_max);
+        if (umma) {
+            c->umma_twist = twist;
+            c->umma_mt = twist ? 1 : umma_tiles(nblk_max);
             c->umma_nblk = nblk_max;
             std::vector<int64_t> off;
             int64_t tot = 0;
@@ -1047,8 +1066,12 @@ int helm_factor(helm_ctx* c) {
                 c->dev_bytes += (size_t)tot;
                 TRY(upload(&c->ufac_off, off.data(), off.size() * sizeof(int64_t), c));
             }
-            launch_repack_umma(c->subs_d, c->subs_h, c->umma_mt, static_cast<const float*>(c->fac),
+            launch_repack_umma(c->subs_d, c->subs_h, c->umma_mt, static_cast<const float*>(c->fac), fac2,
                                c->ufac_off, static_cast<float*>(c->ufac), c->stream);
+        }
+        if (fac2) {
+            CK(cudaStreamSynchronize(c->stream));
+            CK(cudaFree(fac2));
         }
     }
     CK(cudaGetLastError());
@@ -1180,6 +1203,10 @@ int helm_subdomain_solve(helm_ctx* c, int s, int nrhs, const void* R, void* U, i
         launch_solve<double>(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
                              static_cast<const double*>(c->fac), c->Pv64, c->inva64,
                              static_cast<cplx<double>*>(wb), we, DevStatus{c->err_d, c->wait_polls}, c->stream);
+    else if (c->prec == HELM_PREC_TF32 && c->umma_twist)
+        launch_solve_twist(td, 1, c->subs_d, c->umma_nblk, nrhs, static_cast<const float*>(c->ufac),
+                           c->ufac_off, c->Pv32, c->inva32, static_cast<cplx<float>*>(wb), we,
+                           DevStatus{c->err_d, c->wait_polls}, c->stream);
     else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
         launch_solve_umma(td, 1, c->subs_d, c->umma_nblk, nrhs, panel,
                           static_cast<const float*>(c->ufac), c->ufac_off, c->Pv32, c->inva32,

@@ -148,6 +148,11 @@ struct DevProblem {
 void launch_factor_f32(const SubDesc* subs, int nsub, int nbp_max, const DevProblem& P,
                        const float* m32, const cplx<float>* an, const cplx<float>* af,
                        float* fac, int* err, cudaStream_t st);
+// Twisted factors of lines nlines/2 .. nlines-1 (k_factor.cu) into fac2; reads
+// the standard factors of line nlines/2 - 1 from fac.
+void launch_factor_twist_f32(const SubDesc* subs, int nsub, int nbp_max, const DevProblem& P,
+                             const float* m32, const cplx<float>* an, const cplx<float>* af,
+                             const float* fac, float* fac2, int* err, cudaStream_t st);
 void launch_factor_f64(const SubDesc* subs, int nsub, int nbp_max, const DevProblem& P,
                        const double* m64, const cplx<double>* an, const cplx<double>* af,
                        double* fac, int* err, cudaStream_t st);
@@ -183,7 +188,16 @@ int umma_tiles(int nblk_max);
 bool umma_supported(int nblk_max);
 int64_t umma_factor_bytes(const SubDesc& S, int mt);
 void launch_repack_umma(const SubDesc* subs_d, const std::vector<SubDesc>& subs_h, int mt,
-                        const float* fac, const int64_t* dst_off_d, float* dst, cudaStream_t st);
+                        const float* fac, const float* fac2, const int64_t* dst_off_d, float* dst,
+                        cudaStream_t st);  // fac2: twisted factors of lines >= nlines/2, or null
+// Twisted (two-ended) tcgen05 solve: one 2-CTA cluster per (task, panel of 8
+// RHS), top and bottom halves of the lines, all rows per CTA (n <= 256,
+// nlines >= 4); factors repacked with one slice (CR = 1) from the twisted factors.
+bool twist_supported(int nblk_max, int nlines_min);
+void launch_solve_twist(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
+                        const float* afac, const int64_t* afac_off, const cplx<float>* Pv,
+                        const cplx<float>* inva, cplx<float>* buf, int64_t rstride, DevStatus ds,
+                        cudaStream_t st);
 void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
                        int panel, const float* afac, const int64_t* afac_off,
                        const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf,

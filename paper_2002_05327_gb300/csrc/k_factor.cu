@@ -15,6 +15,17 @@
 //
 // One CTA per subdomain; all subdomains are independent and run in one launch.
 // The working matrix lives in the factor storage (L2-resident during its line).
+//
+// Twisted mode (for the two-ended solve of the tensor-core path): with
+// mid = nlines / 2, the lines below mid are eliminated from the far end,
+//     T_{nl-1} = A,   T_j = A_jj - diag(c_j) E_{j+1} diag(c_j),   E_j = T_j^{-1}   (j > mid),
+// and the middle line takes both Schur complements,
+//     M = A_mm - diag(a_m) D_{mid-1} diag(a_m) - diag(c_m) E_{mid+1} diag(c_m),   F = M^{-1},
+// where D_{mid-1} comes from the standard factors.  The operator is complex
+// symmetric, so the coupling of line j to j+1 equals that of j+1 to j
+// (c_j = a_{j+1}, computed from the same face coefficient) and every term uses
+// line j's own stencil.  E_j and F are written to a second array of the same
+// layout (lines mid .. nl-1).
 #include "helm_internal.h"
 
 namespace helm {
@@ -48,7 +59,7 @@ __global__ void __launch_bounds__(512) factor_kernel(const SubDesc* __restrict__
                                                      DevProblem P, const T* __restrict__ m,
                                                      const cplx<T>* __restrict__ an,
                                                      const cplx<T>* __restrict__ af, T* fac,
-                                                     int* err) {
+                                                     T* fac2, int twist, int* err) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     const SubDesc S = subs[blockIdx.x];
     const int ndim = P.ndim;
@@ -80,9 +91,18 @@ __global__ void __launch_bounds__(512) factor_kernel(const SubDesc* __restrict__
     const T omega2 = T(P.omega * P.omega);
     const int nw0 = S.nw[0];
 
-    for (int j = 0; j < S.nlines; ++j) {
-        T* D = fac + S.fac_off + (int64_t)j * 2 * nbp * nbp;
-        const T* Dp = D - (int64_t)2 * nbp * nbp;
+    const int nl = S.nlines, mid = nl / 2;
+    const int nsteps = twist ? nl - mid : nl;
+    const int64_t lstride = (int64_t)2 * nbp * nbp;
+    for (int t = 0; t < nsteps; ++t) {
+        // standard: line t of fac, Schur term from line t-1 of fac;
+        // twisted: lines nl-1 .. mid+1 then mid of fac2
+        const int j = !twist ? t : (t < nl - 1 - mid ? nl - 1 - t : mid);
+        T* D = (twist ? fac2 : fac) + S.fac_off + (int64_t)j * lstride;
+        const T* Dp = fac + S.fac_off + (int64_t)(j - 1) * lstride;                         // D_{j-1}
+        const T* Ep = (twist ? fac2 : fac) + S.fac_off + (int64_t)(j + 1) * lstride;     // E_{j+1}
+        const bool sch_top = !twist ? j > 0 : (j == mid && mid >= 1);
+        const bool sch_bot = twist && j + 1 <= nl - 1;
         // ---- stencil rows of line j
         for (int p = tid; p < n; p += nt) {
             int x[3] = {0, 0, 0};
@@ -121,7 +141,8 @@ __global__ void __launch_bounds__(512) factor_kernel(const SubDesc* __restrict__
                     if (dpq == -nw0) v = sm.off[3 * n + p];
                 }
             }
-            if (j > 0) v = v - sm.acur[p] * get(Dp, nbp, p, q) * sm.cprev[q];
+            if (sch_top) v = v - sm.acur[p] * get(Dp, nbp, p, q) * (twist ? sm.acur[q] : sm.cprev[q]);
+            if (sch_bot) v = v - sm.ccur[p] * get(Ep, nbp, p, q) * sm.ccur[q];
             put(D, nbp, p, q, v);
         }
         __syncthreads();
@@ -210,7 +231,19 @@ static void launch_factor_t(const SubDesc* subs, int nsub, int nbp_max, const De
     size_t smem = sizeof(cplx<T>) * (size_t)(6 + noff) * nbp_max + sizeof(int) * (nbp_max + 2) +
                   (sizeof(T) + sizeof(int)) * nt + 64;
     cudaFuncSetAttribute(factor_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    factor_kernel<T><<<nsub, nt, smem, st>>>(subs, P, m, an, af, fac, err);
+    factor_kernel<T><<<nsub, nt, smem, st>>>(subs, P, m, an, af, fac, nullptr, 0, err);
+}
+
+void launch_factor_twist_f32(const SubDesc* subs, int nsub, int nbp_max, const DevProblem& P,
+                             const float* m32, const cplx<float>* an, const cplx<float>* af,
+                             const float* fac, float* fac2, int* err, cudaStream_t st) {
+    const int nt = 512;
+    const int noff = 2 * (P.ndim - 1);
+    size_t smem = sizeof(cplx<float>) * (size_t)(6 + noff) * nbp_max + sizeof(int) * (nbp_max + 2) +
+                  (sizeof(float) + sizeof(int)) * nt + 64;
+    cudaFuncSetAttribute(factor_kernel<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    factor_kernel<float><<<nsub, nt, smem, st>>>(subs, P, m32, an, af, const_cast<float*>(fac), fac2, 1,
+                                                 err);
 }
 
 void launch_factor_f32(const SubDesc* subs, int nsub, int nbp_max, const DevProblem& P,

@@ -162,7 +162,8 @@ __host__ __device__ inline int64_t umma_line_bytes(int n, int CR, int* nkc) {
 // Repack the column-major factors of every subdomain (k_factor.cu layout) into
 // the swizzled tile image, rounding to TF32.  One thread per output float.
 __global__ void repack_umma_kernel(const SubDesc* __restrict__ subs, const float* __restrict__ fac,
-                                   const int64_t* __restrict__ dst_off, float* dst, int sub, int cr) {
+                                   const float* __restrict__ fac2, const int64_t* __restrict__ dst_off,
+                                   float* dst, int sub, int cr) {
     const SubDesc& S = subs[sub];
     int nkc;
     const int64_t lb = umma_line_bytes(S.nblk, cr, &nkc) / 4;  // floats per line
@@ -185,7 +186,9 @@ __global__ void repack_umma_kernel(const SubDesc* __restrict__ subs, const float
     const int q = k >> 1, part = k & 1;
     float v = 0.f;
     if (p < S.nblk && q < S.nblk) {
-        const float* D = fac + S.fac_off + (int64_t)j * 2 * S.nbp * S.nbp;
+        // lines from nlines/2 on come from the twisted factors when there are any
+        const float* src = (fac2 && j >= S.nlines / 2) ? fac2 : fac;
+        const float* D = src + S.fac_off + (int64_t)j * 2 * S.nbp * S.nbp;
         v = D[(int64_t)q * 2 * S.nbp + part * S.nbp + p];
     }
     dst[dst_off[sub] / 4 + i] = __uint_as_float(to_tf32(v));  // dst_off in bytes
@@ -211,20 +214,20 @@ __device__ __forceinline__ void bulk_s2peer(uint32_t dst, uint32_t src, uint32_t
 // Barriers among the 128 epilogue threads only (named barriers 1 and 2; the
 // producer and issuer warps never take part).  epi_any also ORs a flag over
 // them, so that all four epilogue warps take the same abort decision.
-__device__ __forceinline__ void epi_sync() {
+__device__ __forceinline__ void epi_sync(uint32_t nthreads = 128) {
     __syncwarp();
-    asm volatile("bar.sync 2, 128;" ::: "memory");
+    asm volatile("bar.sync 2, %0;" ::"r"(nthreads) : "memory");
 }
-__device__ __forceinline__ bool epi_any(bool flag) {
+__device__ __forceinline__ bool epi_any(bool flag, uint32_t nthreads = 128) {
     uint32_t out;
     __syncwarp();
     asm volatile(
         "{\n\t.reg .pred q, p;\n\t"
         "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.or.pred p, 1, 128, q;\n\t"
+        "bar.red.or.pred p, 1, %2, q;\n\t"
         "selp.u32 %0, 1, 0, p;\n\t}"
         : "=r"(out)
-        : "r"((uint32_t)flag)
+        : "r"((uint32_t)flag), "r"(nthreads)
         : "memory");
     return out != 0;
 }
@@ -637,10 +640,11 @@ __global__ void __launch_bounds__(kThreads) solve_umma_kernel(
 }
 
 void launch_repack_umma(const SubDesc* subs_d, const std::vector<SubDesc>& subs_h, int mt,
-                        const float* fac, const int64_t* dst_off_d, float* dst, cudaStream_t st) {
+                        const float* fac, const float* fac2, const int64_t* dst_off_d, float* dst,
+                        cudaStream_t st) {
     for (size_t s = 0; s < subs_h.size(); ++s) {
         const int64_t floats = umma_line_bytes(subs_h[s].nblk, mt, nullptr) / 4 * subs_h[s].nlines;
-        repack_umma_kernel<<<(unsigned)((floats + 255) / 256), 256, 0, st>>>(subs_d, fac, dst_off_d,
+        repack_umma_kernel<<<(unsigned)((floats + 255) / 256), 256, 0, st>>>(subs_d, fac, fac2, dst_off_d,
                                                                              dst, (int)s, mt);
     }
 }
@@ -716,6 +720,461 @@ void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nb
     launch_pg<PG_>(tasks, ntask, subs, CR, nblk_max, nrhs, afac, afac_off, Pv, inva, buf, rstride, ds, st)
     if (pg == 32) HELM_UMMA(32); else if (pg == 16) HELM_UMMA(16); else HELM_UMMA(8);
 #undef HELM_UMMA
+}
+
+
+// ============================================================================
+// Twisted (two-ended) block solve on the tensor cores.
+//
+// With the twisted factors (k_factor.cu: D_j = S_j^{-1} for lines j < mid,
+// F = M^{-1} at mid = nl/2, E_j = T_j^{-1} for j > mid) the solve of a
+// subdomain runs as two chains of about nl/2 line steps each, on the two CTAs
+// of a cluster:
+//   top (rank 0):    y_j = D_j (b_j - a_j y_{j-1})                     j = 0 .. mid-1
+//                    u_mid = F (b_mid - a_mid y_{mid-1} - c_mid z_{mid+1})
+//                    u_j = y_j - D_j (c_j u_{j+1})                      j = mid-1 .. 0
+//   bottom (rank 1): z_j = E_j (b_j - c_j z_{j+1})                     j = nl-1 .. mid+1
+//                    u_j = z_j - E_j (a_j u_{j-1})                      j = mid+1 .. nl-1
+// (a_j couples line j to j-1, c_j to j+1; both are diagonal).  The halves meet
+// once in each direction: the bottom sends c_mid z_{mid+1}, the top sends
+// a_{mid+1} u_mid, each as one bulk copy between the CTAs' shared memory.
+// Each CTA holds all n <= 256 rows of the block (two M = 128 tiles), so no
+// data crosses between the CTAs during the line steps, and the chain of a
+// level is about half as long as the one-ended solve's.
+//
+// Roles: warps 0-7 epilogue (warp e: tile e/4, TMEM lanes 32*(e%4) ..);
+// warps 8-9 bulk-copy producers, warps 10-11 MMA issuers, one sub-ring of the
+// operand ring per producer/issuer pair (stream positions q, q+2, ...).
+// Handshakes: full/empty per stage, acc_full per step, b_ready per step (B of
+// the step written; B is single-buffered: the epilogue writes it only after
+// every MMA of the previous step completed), x_in (the peer's middle vector,
+// one phase).  Every wait is bounded; on expiry the CTA raises the device
+// error word, each role leaves its loop, copies and MMAs are drained, the two
+// CTAs drain the middle copies between them, and TMEM is freed.
+constexpr int kTwP = 2;                        // producer / issuer pairs
+constexpr int kTwEpi = 8;                      // epilogue warps (two TMEM tiles)
+constexpr int kTwWarpProd = kTwEpi, kTwWarpIss = kTwWarpProd + kTwP;
+constexpr int kTwThreads = 32 * (kTwWarpIss + kTwP);
+constexpr uint32_t kTwEpiThreads = 32 * kTwEpi;
+
+template <int PG>
+__global__ void __launch_bounds__(kTwThreads) solve_twist_kernel(
+    const Task* __restrict__ tasks, const SubDesc* __restrict__ subs, int nrhs,
+    const float* __restrict__ afac, const int64_t* __restrict__ afac_off,
+    const cplx<float>* __restrict__ Pv, const cplx<float>* __restrict__ inva, cplx<float>* buf,
+    int64_t rstride, int nstage, uint32_t ring_bytes, DevStatus ds) {
+    constexpr int kN = 2 * PG;
+    constexpr int kBChunkBytes = kN * 128;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    const uint32_t rank = cluster_rank();  // 0: top half, 1: bottom half
+    const uint32_t peer = rank ^ 1u;
+    const Task tk = tasks[blockIdx.x / 2];
+    const SubDesc& S = subs[tk.sub];
+    const int n = S.nblk, nl = S.nlines, mid = nl / 2, nb = nl - 1 - mid;
+    const int ntile = (n + 127) / 128;
+    int nkc;
+    const int64_t line_bytes = umma_line_bytes(n, 1, &nkc);
+    const int R = umma_rows(n, 1);
+    const uint32_t stage_bytes = (uint32_t)R * 128;
+    const int NS = nstage, NQ = NS / kTwP;
+    const uint32_t b_bytes = (uint32_t)(nkc * kBChunkBytes);
+    const uint32_t x_bytes = (uint32_t)R * PG * 8;  // middle vector: R rows x PG complex
+    const int nsteps = rank == 0 ? 2 * mid + 1 : 2 * nb;
+    // line of step s of this CTA
+    auto line_of = [&](int st) -> int {
+        if (rank == 0) return st < mid ? st : (st == mid ? mid : 2 * mid - st);
+        return st < nb ? nl - 1 - st : mid + 1 + (st - nb);
+    };
+
+    // shared layout (1024-aligned): ring | B | x_stage | x_in buffer | barriers | slots
+    const uint32_t base = (su32(smem_raw) + 1023u) & ~1023u;
+    unsigned char* gbase = smem_raw + (base - su32(smem_raw));
+    const uint32_t stage0 = base;
+    const uint32_t b0 = stage0 + ring_bytes;
+    float* bl = reinterpret_cast<float*>(gbase + ring_bytes);
+    const uint32_t xs0 = b0 + b_bytes;
+    cplx<float>* xs = reinterpret_cast<cplx<float>*>(gbase + ring_bytes + b_bytes);
+    const uint32_t xi0 = xs0 + x_bytes;
+    const cplx<float>* xi = reinterpret_cast<const cplx<float>*>(gbase + ring_bytes + b_bytes + x_bytes);
+    const uint32_t bars = (xi0 + x_bytes + 7u) & ~7u;
+    uint64_t* bars_g = reinterpret_cast<uint64_t*>(gbase + (bars - base));
+    auto full = [&](int s) { return bars + 8u * s; };
+    auto empty = [&](int s) { return bars + 8u * (NS + s); };
+    const uint32_t acc_full = bars + 8u * (2 * NS);
+    const uint32_t b_ready = bars + 8u * (2 * NS + 1);
+    const uint32_t x_in = bars + 8u * (2 * NS + 2);
+    const uint32_t drain = bars + 8u * (2 * NS + 3);
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars_g + 2 * NS + 4);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+    volatile int* x_sent = reinterpret_cast<volatile int*>(tmem_slot + 2);  // this CTA sent its middle copy
+    volatile int* x_peer = reinterpret_cast<volatile int*>(tmem_slot + 3);  // the peer sent its (exit)
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    constexpr uint32_t kCols = 2 * kTwP * kN <= 32 ? 32 : 2 * kTwP * kN <= 64 ? 64 :
+                               2 * kTwP * kN <= 128 ? 128 : 256;  // tile t, issuer q: (t*kTwP + q)*kN
+
+    if (tid == 0) {
+        *abort_flag = 0;
+        *x_sent = 0;
+        *x_peer = 0;
+        for (int s = 0; s < NS; ++s) {
+            mb_init(full(s), 1);
+            mb_init(empty(s), 1);
+        }
+        mb_init(acc_full, kTwP);
+        mb_init(b_ready, 1);
+        mb_init(x_in, 1);
+        mb_init(drain, kTwP);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (uint32_t i = tid; i < b_bytes / 4; i += blockDim.x) bl[i] = 0.f;
+    {
+        float* sg = reinterpret_cast<float*>(gbase);
+        for (uint32_t i = tid; i < ring_bytes / 4; i += blockDim.x) sg[i] = 0.f;
+    }
+    if (warp == kTwWarpIss) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(kCols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync();  // the peer's barriers are initialised before its copy can land
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+    // arm x_in for the peer's single middle copy (it may land before or after)
+    if (tid == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(x_in), "r"(x_bytes) : "memory");
+
+    if (warp >= kTwWarpProd && warp < kTwWarpProd + kTwP) {
+        // ====================================================== producers
+        const int pq = warp - kTwWarpProd;
+        if (lane == 0) {
+            const char* abase = reinterpret_cast<const char*>(afac) + afac_off[tk.sub];
+            int k = 0;
+            for (int step = 0; step < nsteps && !*abort_flag; ++step) {
+                const int j = line_of(step);
+                for (int li = pq; li < nkc; li += kTwP) {
+                    const int s = pq * NQ + k % NQ;
+                    if (k >= NQ && !mb_wait(empty(s), (uint32_t)(((k / NQ) - 1) & 1), ds.polls)) {
+                        atomicExch(ds.err, 2);
+                        *abort_flag = 1;
+                    }
+                    if (*abort_flag) break;
+                    mb_expect_tx(full(s), stage_bytes);
+                    bulk_g2s(stage0 + s * stage_bytes, abase + (int64_t)j * line_bytes + (int64_t)li * stage_bytes,
+                             stage_bytes, full(s));
+                    ++k;
+                }
+            }
+            for (int kk = (k > NQ ? k - NQ : 0); kk < k; ++kk)
+                mb_wait(full(pq * NQ + kk % NQ), (uint32_t)((kk / NQ) & 1), kWait);
+        }
+    } else if (warp >= kTwWarpIss && warp < kTwWarpIss + kTwP) {
+        // ====================================================== MMA issuers
+        const int q = warp - kTwWarpIss;
+        if (lane == 0) {
+            constexpr uint32_t idesc = idesc_tf32(128, kN);
+            const uint64_t bdesc0 = desc_sw128(b0);
+            int k = 0;
+            for (int step = 0; step < nsteps && !*abort_flag; ++step) {
+                if (!mb_wait(b_ready, (uint32_t)(step & 1), ds.polls)) {
+                    atomicExch(ds.err, 2);
+                    *abort_flag = 1;
+                    break;
+                }
+                tc_fence_after();
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                bool first = true;
+                for (int li = q; li < nkc; li += kTwP) {
+                    const int s = q * NQ + k % NQ;
+                    const uint32_t par = (uint32_t)((k / NQ) & 1);
+                    ++k;
+                    if (!mb_wait(full(s), par, ds.polls)) {
+                        atomicExch(ds.err, 2);
+                        *abort_flag = 1;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint64_t bdesc = bdesc0 + (uint64_t)(li * (kBChunkBytes >> 4));
+                    for (int t = 0; t < ntile; ++t) {
+                        const uint64_t adesc = desc_sw128(stage0 + s * stage_bytes + (uint32_t)t * kTileBytes);
+                        const uint32_t dacc = tmem + (uint32_t)((t * kTwP + q) * kN);
+#pragma unroll
+                        for (int kk = 0; kk < 4; ++kk)
+                            umma_tf32(dacc, adesc + (uint64_t)(2 * kk), bdesc + (uint64_t)(2 * kk), idesc,
+                                      (first && kk == 0) ? 0u : 1u);
+                    }
+                    first = false;
+                    umma_commit(empty(s));
+                }
+                if (*abort_flag) break;
+                umma_commit(acc_full);
+            }
+            umma_commit(drain);
+            mb_wait(drain, 0u, kWait);
+        }
+    } else if (warp < kTwEpi) {
+        // ====================================================== epilogue (warps 0-7)
+        const int t = warp / 4, quarter = warp % 4;
+        const int p = t * 128 + quarter * 32 + lane;  // block row (TMEM lane quarter*32 + lane of tile t)
+        const bool rv = p < n && t < ntile;
+        const int n4 = (n + 3) & ~3;
+        const bool wr = p < n4 && t < ntile;  // writes B rows 2p, 2p+1
+        const cplx<float> pvp = rv ? Pv[S.coup_off + p] : mk<float>(0, 0);
+        const cplx<float>* ia = inva + S.inva_off;
+        cplx<float>* V = buf + tk.buf_off;
+        const int c0 = blockIdx.y * PG;
+        int ncol = nrhs - c0;
+        if (ncol > PG) ncol = PG;
+        const int k0 = 2 * p;
+        const int kcb = k0 / kChunkK, kkb = k0 % kChunkK;
+        auto boff = [&](int row) -> uint32_t {
+            const int chunk = (kkb / 4) ^ (row % 8);
+            return (uint32_t)(kcb * kBChunkBytes + row * 128 + chunk * 16 + (kkb % 4) * 4);
+        };
+        auto coup = [&](int face) -> cplx<float> { return rv ? pvp * ia[face] : mk<float>(0, 0); };
+        auto vload = [&](int j, cplx<float> (&dst)[PG]) {
+#pragma unroll
+            for (int c = 0; c < PG; ++c)
+                dst[c] = (rv && c < ncol && j >= 0) ? V[(int64_t)(c0 + c) * rstride + (int64_t)j * n + p]
+                                                    : mk<float>(0, 0);
+        };
+        auto vstore = [&](int j, const cplx<float> (&v)[PG]) {
+#pragma unroll
+            for (int c = 0; c < PG; ++c)
+                if (rv && c < ncol) V[(int64_t)(c0 + c) * rstride + (int64_t)j * n + p] = v[c];
+        };
+        // B of the next step: rows 2c (Re r, -Im r) and 2c+1 (Im r, Re r), TF32; then
+        // (writers' stores before the tensor cores' reads, TMEM loads before the
+        // thread sync) one arrival on b_ready
+        auto announce = [&](const cplx<float> (&v)[PG]) {
+            if (wr) {
+#pragma unroll
+                for (int c = 0; c < PG; ++c) {
+                    const float re = __uint_as_float(to_tf32(v[c].re)), im = __uint_as_float(to_tf32(v[c].im));
+                    const float nim = __uint_as_float(to_tf32(-v[c].im));
+                    *reinterpret_cast<float2*>(bl + boff(2 * c) / 4) = make_float2(re, nim);
+                    *reinterpret_cast<float2*>(bl + boff(2 * c + 1) / 4) = make_float2(im, re);
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            tc_fence_before();
+            epi_sync(kTwEpiThreads);
+            if (tid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b_ready) : "memory");
+        };
+        // middle vector to the peer: rows of this CTA into x_stage, one bulk copy
+        auto send_middle = [&](const cplx<float> (&v)[PG]) {
+            if (p < R) {
+#pragma unroll
+                for (int c = 0; c < PG; ++c) xs[p * PG + c] = v[c];
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            epi_sync(kTwEpiThreads);
+            if (tid == 0) {
+                bulk_s2peer(map_peer(xi0, peer), xs0, x_bytes, map_peer(x_in, peer));
+                *x_sent = 1;
+            }
+        };
+        // the peer's middle vector (every epilogue thread waits; uniform outcome)
+        auto recv_middle = [&](cplx<float> (&dst)[PG]) -> bool {
+            const bool got = mb_wait(x_in, 0u, ds.polls);
+            if (epi_any(!got, kTwEpiThreads)) return false;
+#pragma unroll
+            for (int c = 0; c < PG; ++c) dst[c] = (p < R) ? xi[p * PG + c] : mk<float>(0, 0);
+            return true;
+        };
+        // operand kept from memory for the epilogue of step st: top: b_{st+1}
+        // (forward), y_j (backward); bottom: b_{j-1} (forward), z_j (backward)
+        auto pre_line = [&](int st) -> int {
+            if (st >= nsteps) return -1;
+            if (rank == 0) return st < mid ? st + 1 : (st == mid ? -1 : 2 * mid - st);
+            if (st < nb) return (nl - 2 - st > mid) ? nl - 2 - st : -1;
+            return mid + 1 + (st - nb);
+        };
+        cplx<float> pre[PG], pre_next[PG], outv[PG], nbv[PG], xv[PG];
+        bool ok = true;
+        // first B: b_0 (top) or b_{nl-1} (bottom)
+        vload(rank == 0 ? 0 : nl - 1, nbv);
+        vload(pre_line(0), pre);
+        announce(nbv);
+        for (int step = 0; step < nsteps; ++step) {
+            const int j = line_of(step);
+            vload(pre_line(step + 1), pre_next);
+            bool bad = *abort_flag || !mb_wait(acc_full, (uint32_t)(step & 1), ds.polls);
+            if (epi_any(bad, kTwEpiThreads)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            float acc[kN];
+#pragma unroll
+            for (int e = 0; e < kN; ++e) acc[e] = 0.f;
+            {
+                uint32_t part[kTwP][kN / 16][16];
+#pragma unroll
+                for (int q = 0; q < kTwP; ++q)
+#pragma unroll
+                    for (int h = 0; h < kN / 16; ++h)
+                        if (q < nkc)
+                            tmem_ld16_async(tmem + ((uint32_t)(quarter * 32) << 16) +
+                                                (uint32_t)(((t < ntile ? t : 0) * kTwP + q) * kN + 16 * h),
+                                            part[q][h]);
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+                for (int q = 0; q < kTwP; ++q)
+#pragma unroll
+                    for (int h = 0; h < kN / 16; ++h) {
+                        if (q >= nkc) continue;
+                        tmem_pin16(part[q][h]);
+#pragma unroll
+                        for (int e = 0; e < 16; ++e) acc[16 * h + e] += __uint_as_float(part[q][h][e]);
+                    }
+            }
+            cplx<float> y[PG];
+#pragma unroll
+            for (int c = 0; c < PG; ++c) y[c] = mk<float>(acc[2 * c], acc[2 * c + 1]);
+            bool last = step + 1 >= nsteps;
+            if (rank == 0) {
+                if (step < mid) {  // y_j; next: b_{j+1} - a_{j+1} y_j (minus the bottom's c_mid z_{mid+1} at mid)
+                    const cplx<float> a = coup(j + 1);
+#pragma unroll
+                    for (int c = 0; c < PG; ++c) {
+                        outv[c] = y[c];
+                        nbv[c] = rv ? pre[c] - a * y[c] : mk<float>(0, 0);
+                    }
+                    if (step + 1 == mid) {
+                        if (!recv_middle(xv)) { ok = false; break; }
+#pragma unroll
+                        for (int c = 0; c < PG; ++c) nbv[c] = rv ? nbv[c] - xv[c] : mk<float>(0, 0);
+                    }
+                } else if (step == mid) {  // u_mid; send a_{mid+1} u_mid; next: c_{mid-1} u_mid
+                    const cplx<float> a = coup(mid + 1), cc = coup(mid);
+                    cplx<float> snd[PG];
+#pragma unroll
+                    for (int c = 0; c < PG; ++c) {
+                        outv[c] = y[c];
+                        snd[c] = rv ? a * y[c] : mk<float>(0, 0);
+                        nbv[c] = rv ? cc * y[c] : mk<float>(0, 0);
+                    }
+                    if (nb > 0) send_middle(snd);
+                } else {  // u_j = y_j - D_j (c_j u_{j+1}); next: c_{j-1} u_j
+                    const cplx<float> cc = coup(j);
+#pragma unroll
+                    for (int c = 0; c < PG; ++c) {
+                        outv[c] = pre[c] - y[c];
+                        nbv[c] = rv ? cc * outv[c] : mk<float>(0, 0);
+                    }
+                }
+            } else {
+                if (step < nb) {  // z_j; next: b_{j-1} - c_{j-1} z_j, or at mid+1: the top's a_{mid+1} u_mid
+                    const cplx<float> cc = coup(j);
+#pragma unroll
+                    for (int c = 0; c < PG; ++c) {
+                        outv[c] = y[c];
+                        nbv[c] = rv ? pre[c] - cc * y[c] : mk<float>(0, 0);
+                    }
+                    if (step + 1 == nb) {
+                        cplx<float> snd[PG];
+                        const cplx<float> cm = coup(mid + 1);  // c_mid couples line mid to mid+1
+#pragma unroll
+                        for (int c = 0; c < PG; ++c) snd[c] = rv ? cm * y[c] : mk<float>(0, 0);
+                        send_middle(snd);
+                        if (!recv_middle(xv)) { ok = false; break; }
+#pragma unroll
+                        for (int c = 0; c < PG; ++c) {
+                            nbv[c] = rv ? xv[c] : mk<float>(0, 0);
+                            pre_next[c] = y[c];  // z_{mid+1}, the first backward step's y
+                        }
+                    }
+                } else {  // u_j = z_j - E_j (a_j u_{j-1}); next: a_{j+1} u_j
+                    const cplx<float> a = coup(j + 1);
+#pragma unroll
+                    for (int c = 0; c < PG; ++c) {
+                        outv[c] = pre[c] - y[c];
+                        nbv[c] = rv ? a * outv[c] : mk<float>(0, 0);
+                    }
+                }
+            }
+            if (!last) announce(nbv);
+            vstore(j, outv);
+#pragma unroll
+            for (int c = 0; c < PG; ++c) pre[c] = pre_next[c];
+        }
+        if (!ok) {
+            atomicExch(ds.err, 2);
+            *abort_flag = 1;
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    // Drain the middle copies before either CTA leaves: each learns whether
+    // its peer sent one, waits until it has landed, and the second cluster
+    // barrier keeps each CTA resident until its own copy has been read.
+    if (tid == 0) {
+        const uint32_t dst = map_peer(su32((const void*)x_peer), peer);
+        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(dst), "r"((uint32_t)*x_sent) : "memory");
+    }
+    __syncwarp();
+    cluster_sync();
+    if (tid == 0 && *x_peer && !mb_wait(x_in, 0u, kWait)) atomicExch(ds.err, 2);
+    __syncwarp();
+    cluster_sync();
+    tc_fence_after();
+    if (warp == kTwWarpIss)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kCols) : "memory");
+}
+
+// Shared-memory plan of a twisted launch: ns stages (kTwP sub-rings of at
+// least 2) of R*128 bytes plus the 256-row tail of the last one, B, the two
+// middle buffers, barriers and slots, alignment; 0 if it does not fit.
+static size_t twist_smem_plan(int PG, int nblk_max, int* ns_out, uint32_t* ring_out) {
+    int nkc = 0;
+    umma_line_bytes(nblk_max, 1, &nkc);
+    const size_t sb = (size_t)umma_rows(nblk_max, 1) * 128;
+    const size_t tail = 2 * (size_t)kTileBytes;  // the second tile's MMA reads 128 rows from +16 KB
+    const size_t fixed = (size_t)nkc * 2 * PG * 128 + 2 * (size_t)umma_rows(nblk_max, 1) * PG * 8 + 1024 + 1024;
+    const size_t budget = 227 * 1024;
+    if (fixed + (2 * kTwP - 1) * sb + tail > budget) return 0;
+    int ns = (int)((budget - fixed - tail) / sb) + 1;
+    if (ns > 32) ns = 32;
+    ns -= ns % kTwP;
+    *ns_out = ns;
+    *ring_out = (uint32_t)((ns - 1) * sb + tail);
+    return *ring_out + fixed;
+}
+
+bool twist_supported(int nblk_max, int nlines_min) {
+    int ns;
+    uint32_t ring;
+    return nblk_max <= 256 && nlines_min >= 4 && twist_smem_plan(8, nblk_max, &ns, &ring) != 0;
+}
+
+void launch_solve_twist(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
+                        const float* afac, const int64_t* afac_off, const cplx<float>* Pv,
+                        const cplx<float>* inva, cplx<float>* buf, int64_t rstride, DevStatus ds,
+                        cudaStream_t st) {
+    if (ntask == 0) return;
+    constexpr int PG = 8;
+    int ns = 0;
+    uint32_t ring = 0;
+    const size_t smem = twist_smem_plan(PG, nblk_max, &ns, &ring);
+    cudaFuncSetAttribute(solve_twist_kernel<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(ntask * 2, (nrhs + PG - 1) / PG, 1);
+    cfg.blockDim = dim3(kTwThreads, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, solve_twist_kernel<PG>, tasks, subs, nrhs, afac, afac_off, Pv, inva, buf, rstride,
+                       ns, ring, ds);
 }
 
 }  // namespace helm

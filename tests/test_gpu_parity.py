@@ -26,7 +26,8 @@ from oracle import helmholtz as OH
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-10, 1: 1e-3, 2: 3e-2, 3: 3e-2}
+TOL = {0: 1e-10, 1: 1e-3, 2: 3e-2, 3: 3e-2, 4: 3e-2}
+PRECS = [0, 1, 2, 3, 4]
 
 
 @pytest.fixture(scope="module")
@@ -46,9 +47,13 @@ def rel(a, b):
 
 def _ctx(H, wl, prec, **kw):
     """prec 0/1/2 = FP64 / complex64 / TF32 tensor cores (tcgen05 where the
-    blocks allow it); 3 = TF32 forced onto the mma.sync kernel."""
+    blocks allow it, in the twisted two-ended form where every subdomain has
+    at least 4 lines); 3 = TF32 forced onto the mma.sync kernel; 4 = TF32 on
+    the one-ended tcgen05 kernel."""
     if prec == 3:
         prec, kw = 2, dict(kw, tc_kernel=1)
+    elif prec == 4:
+        prec, kw = 2, dict(kw, tc_kernel=2)
     c = H.helm_setup_workload(wl, precision=prec, **kw)
     H.helm_factor(c)
     return c
@@ -76,7 +81,7 @@ def _nonuniform():
 CASES["2d-nonuniform-3x3"] = _nonuniform
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_apply_ddm_matches_algorithm(H, case, prec):
     """helm_apply_ddm equals the oracle's Algorithm 3.1 / 4.1 (same windows,
@@ -89,7 +94,7 @@ def test_apply_ddm_matches_algorithm(H, case, prec):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", PRECS)
 def test_subdomain_solve_matches_local_direct_solve(H, prec):
     wl = W.small_2d(nx=60, ny=52, nbx=4, nby=3, nrhs=3)
     ctx = _ctx(H, wl, prec)
@@ -103,7 +108,7 @@ def test_subdomain_solve_matches_local_direct_solve(H, prec):
         R = rng.standard_normal((3,) + sub.shape) + 1j * rng.standard_normal((3,) + sub.shape)
         u = H.helm_subdomain_solve(ctx, s, R)
         ref = part.local_solve(sub, R)
-        assert rel(u, ref) < {0: 1e-11, 1: 1e-4, 2: 1e-2, 3: 1e-2}[prec], (s, rel(u, ref))
+        assert rel(u, ref) < {0: 1e-11, 1: 1e-4, 2: 1e-2, 3: 1e-2, 4: 1e-2}[prec], (s, rel(u, ref))
     ctx.close()
 
 
@@ -120,7 +125,7 @@ def test_config1_ddm_fp64(H):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", PRECS)
 def test_gmres_reaches_global_solution(H, prec):
     wl = W.small_2d(nx=64, ny=56, nbx=3, nby=3, pml=10, overlap=4, sub_pml=10, nrhs=3)
     ctx = _ctx(H, wl, prec)
@@ -186,7 +191,7 @@ def test_errors_are_reported(H):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", [0, 1, 2, 3])
+@pytest.mark.parametrize("prec", PRECS)
 def test_expired_wait_is_reported_and_context_stays_usable(H, prec):
     """wait_limit=-1 makes every ordinary bounded wait inside the subdomain-solve
     kernels give up at its first check, so each kernel takes its abort path:
@@ -228,12 +233,15 @@ def test_deterministic_and_device_pointers(H):
     ctx.close()
 
 
-def test_cluster_tensor_core_path_is_deterministic(H):
-    """Blocks of more than 128 rows run as 2-CTA clusters exchanging the B
-    operand through distributed shared memory; repeated applications must be
-    bitwise identical (a handshake race would show as run-to-run changes)."""
+@pytest.mark.parametrize("prec", [2, 4])
+def test_cluster_tensor_core_path_is_deterministic(H, prec):
+    """The tcgen05 solves run as 2-CTA clusters: the twisted form (prec 2)
+    hands the middle line's vectors between its two halves, the one-ended form
+    (prec 4, blocks of more than 128 rows) exchanges the B operand every line
+    step.  Repeated applications must be bitwise identical (a handshake race
+    would show as run-to-run changes)."""
     wl = CASES["2d-wide-2x2"]()
-    ctx = _ctx(H, wl, 2)
+    ctx = _ctx(H, wl, prec)
     u1 = H.helm_apply_ddm(ctx, wl.f)
     for _ in range(3):
         assert np.array_equal(H.helm_apply_ddm(ctx, wl.f), u1)

@@ -751,7 +751,7 @@ void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nb
 // one phase).  Every wait is bounded; on expiry the CTA raises the device
 // error word, each role leaves its loop, copies and MMAs are drained, the two
 // CTAs drain the middle copies between them, and TMEM is freed.
-constexpr int kTwP = 2;                        // producer / issuer pairs
+constexpr int kTwP = 3;                        // producer / issuer pairs
 constexpr int kTwEpi = 8;                      // epilogue warps (two TMEM tiles)
 constexpr int kTwWarpProd = kTwEpi, kTwWarpIss = kTwWarpProd + kTwP;
 constexpr int kTwThreads = 32 * (kTwWarpIss + kTwP);

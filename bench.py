@@ -35,10 +35,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "RHS solves/sec at 1e-6 rel. L2 (mixed vs plain FP64 GPU DDM); %tensor/HBM roofline"
-# DRAM bytes (read + write) per launch of the tcgen05 solve kernel, averaged over the 252
+# DRAM bytes (read + write) per launch of the tensor-core solve kernel, averaged over the
 # solve launches of one step of this workload, from one single-pass ncu capture
-# (profiles/launches_2d-layered-1064sq-64rhs.md).  Set to None when the kernel changes.
-SOLVE_TRAFFIC_BYTES_PER_LAUNCH = None
+# (profiles/launches_2d-layered-1064sq-64rhs.md), per --prec.  An entry is removed when
+# the kernel changes.
+SOLVE_TRAFFIC_BYTES_PER_LAUNCH = {}
 UNIT = "RHS/s"
 
 
@@ -54,7 +55,7 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--workload", type=int, default=2, help="workload number (2 = bench)")
-    ap.add_argument("--prec", default="tf32", choices=["tf32", "mixed"],
+    ap.add_argument("--prec", default="f16", choices=["f16", "tf32", "mixed"],
                     help="precision of the subdomain factors/solves of the product path")
     ap.add_argument("--nrhs", type=int, default=0,
                     help="use only the first NRHS sources (profiling runs); 0 = all")
@@ -225,7 +226,7 @@ def main():
 
     # ---------------- mixed precision (the product path)
     stream = torch.cuda.current_stream(dev).cuda_stream
-    prec = H.HELM_PREC_TF32 if args.prec == "tf32" else H.HELM_PREC_MIXED
+    prec = {"f16": H.HELM_PREC_F16, "tf32": H.HELM_PREC_TF32, "mixed": H.HELM_PREC_MIXED}[args.prec]
     ctx = H.helm_setup_workload(wl, precision=prec, profile=1, stream=stream)
     t0 = time.time()
     H.helm_factor(ctx)
@@ -324,27 +325,29 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "tf32" if args.prec == "tf32" else "c64",
+        "vs_baseline": None, "dtype": {"f16": "f16", "tf32": "tf32", "mixed": "c64"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": wl.name, "grid": list(wl.N), "h_m": wl.h, "freq_hz": 15,
+        "config": {"workload": wl.name, "grid": list(wl.N), "h_m": wl.h,
+                   "freq_hz": round(wl.omega / (2 * np.pi), 6),
                    "nb": list(wl.nb), "overlap": wl.overlap, "sub_pml": wl.sub_pml,
                    "nrhs": nrhs, "rtol": args.rtol, "outer": "FP64 flexible GMRES",
-                   "subdomain_precision": ("complex64 factors, TF32 tensor-core block products, "
-                                           "FP32 accumulation") if args.prec == "tf32"
-                   else "complex64 factors and FP32 block products",
+                   "subdomain_precision": {
+                       "f16": "complex64 factors, FP16 tensor-core operands with power-of-two scales "
+                              "per factor line and right-hand-side column, FP32 accumulation",
+                       "tf32": "complex64 factors, TF32 tensor-core block products, FP32 accumulation",
+                       "mixed": "complex64 factors and FP32 block products"}[args.prec],
                    "l2": "inputs larger than L2 (device working set %.1f GB, RHS %.2f GB)" % (
                        dev_bytes / 1e9, nrhs * np.prod(wl.N) * 16 / 1e9),
                    "parallelism": "replicas" if world > 1 else "single"},
         "gmres": {"iters": iters, "applications": apps, "max_rel_resid": res,
                   "factor_ms": factor_ms, "levels": stats[0]["levels"],
                   "subdomain_solves_per_application": stats[0]["solves"]},
-        "roofline": {"kernel": ("solve_twist_kernel" if args.prec == "tf32" else "solve_kernel")
+        "roofline": {"kernel": ("solve_twist_kernel" if args.prec in ("tf32", "f16") else "solve_kernel")
                      + " (subdomain forward/backward block solves)",
                      "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
                      "frac": achieved / hbm,
-                     "traffic": (SOLVE_TRAFFIC_BYTES_PER_LAUNCH
-                                 if SOLVE_TRAFFIC_BYTES_PER_LAUNCH and args.prec == "tf32"
-                                 and args.workload == 2 and not args.nrhs else None),
+                     "traffic": (SOLVE_TRAFFIC_BYTES_PER_LAUNCH.get(args.prec)
+                                 if args.workload == 2 and not args.nrhs else None),
                      "traffic_unit": "bytes per launch", "peak_source": peak_src,
                      "tflops_achieved": tflops,
                      "bytes_per_launch": sol["bytes"] / max(1, sol["launches"]),

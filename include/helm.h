@@ -57,8 +57,12 @@ enum helm_status {
 enum helm_precision {
     HELM_PREC_F64 = 0,   /* complex128 factors and local solves (plain FP64 DDM) */
     HELM_PREC_MIXED = 1, /* complex64 factors and local solves, FP64 outer GMRES */
-    HELM_PREC_TF32 = 2   /* complex64 factors, local block products on the tensor
+    HELM_PREC_TF32 = 2,  /* complex64 factors, local block products on the tensor
                             cores in TF32 with FP32 accumulation, FP64 outer GMRES */
+    HELM_PREC_F16 = 3    /* as HELM_PREC_TF32, but where the two-ended tensor-core solve
+                            applies its operands are FP16 (the same 10-bit mantissa as
+                            TF32) with power-of-two scales per factor line and per
+                            right-hand-side column, half the bytes and MMAs */
 };
 
 enum helm_pml_form {

@@ -28,6 +28,7 @@ HELM_ERR_NUMERIC = -7
 HELM_PREC_F64 = 0
 HELM_PREC_MIXED = 1
 HELM_PREC_TF32 = 2
+HELM_PREC_F16 = 3
 HELM_PML_LITERAL = 0
 HELM_PML_OMEGA = 1
 HELM_MEM_HOST = 0

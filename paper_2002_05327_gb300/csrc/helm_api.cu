@@ -136,6 +136,9 @@ struct helm_ctx {
     int umma_mt = 0;                   // CTAs per block in the tcgen05 solve (0: not used)
     int umma_nblk = 0;                 // largest block of the tcgen05 solve
     bool umma_twist = false;           // tcgen05 solve in its twisted (two-ended) form
+    bool f16 = false;                  // HELM_PREC_F16: FP16 operands in the twisted solve
+    int* ascale_d = nullptr;           // per (subdomain, line) exponent of the FP16 factor scale
+    size_t inva_count = 0;             // entries of inva (nlines + 1 per subdomain)
     void* fac = nullptr;
     size_t fac_bytes = 0;
     bool factored = false;
@@ -363,6 +366,10 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
     c->prec = HELM_PREC_MIXED;
     if (cfg && (cfg->precision == HELM_PREC_F64 || cfg->precision == HELM_PREC_TF32))
         c->prec = cfg->precision;
+    if (cfg && cfg->precision == HELM_PREC_F16) {  // TF32 everywhere else, FP16 in the twisted solve
+        c->prec = HELM_PREC_TF32;
+        c->f16 = true;
+    }
     if (c->cfg.restart <= 0) c->cfg.restart = 30;
     if (c->cfg.restart > 63) return fail(HELM_ERR_ARG, "restart must be at most 63");
     if (c->cfg.wait_limit < -1) return fail(HELM_ERR_ARG, "wait_limit must be -1, 0 or positive");
@@ -555,6 +562,7 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
         TRY(upload(&c->af32, f64.data(), f64.size() * 8, c));
         TRY(upload(&c->Pv32, p64.data(), p64.size() * 8, c));
         TRY(upload(&c->inva32, i64.data(), i64.size() * 8, c));
+        c->inva_count = ia.size();
     }
     {
         std::vector<double> t64(P.d + 1);
@@ -729,9 +737,9 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
             }
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
             if (c->prec == HELM_PREC_TF32 && c->umma_twist)
-                launch_solve_twist(t, nt, c->subs_d, c->umma_nblk, nrhs, static_cast<const float*>(c->ufac),
-                                   c->ufac_off, c->Pv32, c->inva32, buf, rs,
-                                   DevStatus{c->err_d, c->wait_polls}, c->stream);
+                launch_solve_twist(t, nt, c->subs_d, c->umma_nblk, nrhs, c->ufac, c->ufac_off, c->ascale_d,
+                                   c->f16, c->Pv32, c->inva32, buf, rs, DevStatus{c->err_d, c->wait_polls},
+                                   c->stream);
             else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
                 launch_solve_umma(t, nt, c->subs_d, c->umma_nblk, nrhs, panel,
                                   static_cast<const float*>(c->ufac), c->ufac_off, c->Pv32,
@@ -1055,19 +1063,33 @@ int helm_factor(helm_ctx* c) {
             c->umma_twist = twist;
             c->umma_mt = twist ? 1 : umma_tiles(nblk_max);
             c->umma_nblk = nblk_max;
+            const bool f16 = twist && c->f16;
             std::vector<int64_t> off;
             int64_t tot = 0;
+            int max_lines = 0;
             for (const SubDesc& S : c->subs_h) {
                 off.push_back(tot);
-                tot += umma_factor_bytes(S, c->umma_mt);
+                tot += f16 ? twist_f16_factor_bytes(S) : umma_factor_bytes(S, c->umma_mt);
+                max_lines = std::max(max_lines, S.nlines);
             }
             if (!c->ufac) {
                 CK(cudaMalloc(&c->ufac, (size_t)tot));
                 c->dev_bytes += (size_t)tot;
                 TRY(upload(&c->ufac_off, off.data(), off.size() * sizeof(int64_t), c));
             }
-            launch_repack_umma(c->subs_d, c->subs_h, c->umma_mt, static_cast<const float*>(c->fac), fac2,
-                               c->ufac_off, static_cast<float*>(c->ufac), c->stream);
+            if (f16) {
+                if (!c->ascale_d) {
+                    CK(cudaMalloc(&c->ascale_d, c->inva_count * sizeof(int)));
+                    c->dev_bytes += c->inva_count * sizeof(int);
+                }
+                launch_line_scales(c->subs_d, c->P.nsub, max_lines, static_cast<const float*>(c->fac), fac2,
+                                   c->ascale_d, c->stream);
+                launch_repack_f16(c->subs_d, c->subs_h, static_cast<const float*>(c->fac), fac2, c->ascale_d,
+                                  c->ufac_off, c->ufac, c->stream);
+            } else {
+                launch_repack_umma(c->subs_d, c->subs_h, c->umma_mt, static_cast<const float*>(c->fac), fac2,
+                                   c->ufac_off, static_cast<float*>(c->ufac), c->stream);
+            }
         }
         if (fac2) {
             CK(cudaStreamSynchronize(c->stream));
@@ -1204,8 +1226,8 @@ int helm_subdomain_solve(helm_ctx* c, int s, int nrhs, const void* R, void* U, i
                              static_cast<const double*>(c->fac), c->Pv64, c->inva64,
                              static_cast<cplx<double>*>(wb), we, DevStatus{c->err_d, c->wait_polls}, c->stream);
     else if (c->prec == HELM_PREC_TF32 && c->umma_twist)
-        launch_solve_twist(td, 1, c->subs_d, c->umma_nblk, nrhs, static_cast<const float*>(c->ufac),
-                           c->ufac_off, c->Pv32, c->inva32, static_cast<cplx<float>*>(wb), we,
+        launch_solve_twist(td, 1, c->subs_d, c->umma_nblk, nrhs, c->ufac, c->ufac_off, c->ascale_d, c->f16,
+                           c->Pv32, c->inva32, static_cast<cplx<float>*>(wb), we,
                            DevStatus{c->err_d, c->wait_polls}, c->stream);
     else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
         launch_solve_umma(td, 1, c->subs_d, c->umma_nblk, nrhs, panel,
@@ -1310,7 +1332,7 @@ void helm_destroy(helm_ctx* c) {
     void* ptrs[] = {c->ufac, c->ufac_off, c->subs_d, c->g_alpha, c->m64, c->m32, c->an64, c->af64, c->an32, c->af32,
                     c->Pv64, c->inva64, c->Pv32, c->inva32, c->tab64, c->tab32, c->box_of,
                     c->fac, c->err_d, c->tasks_d, c->inc_d, c->node_buf_d, c->buf, c->bvec,
-                    c->small_d, c->partial_d, c->scal_d, c->vptr_d, c->zptr_d};
+                    c->small_d, c->partial_d, c->scal_d, c->vptr_d, c->zptr_d, c->ascale_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto* p : c->gm) cudaFree(p);

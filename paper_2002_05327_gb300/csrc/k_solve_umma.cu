@@ -44,6 +44,8 @@
 // the CTA exits.
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "helm_internal.h"
 
 namespace helm {
@@ -100,6 +102,23 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
 __host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
            ((uint32_t)(M >> 4) << 24);
+}
+// Instruction descriptor, kind::f16 with FP16 A and B (K-major), D f32.
+__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
+    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void umma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.u32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+// 2^e as a float for -126 <= e <= 127 (0 below)
+__device__ __forceinline__ float pow2f(int e) {
+    return e < -126 ? 0.f : __int_as_float((e > 127 ? 127 + 127 : e + 127) << 23);
 }
 __device__ __forceinline__ void umma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
                                           uint32_t idesc, uint32_t accumulate) {
@@ -159,6 +178,15 @@ __host__ __device__ inline int64_t umma_line_bytes(int n, int CR, int* nkc) {
     return (int64_t)kc * CR * umma_rows(n, CR) * 128;
 }
 
+// FP16 image for the twisted solve (one slice, all rows): K chunks of 64
+// values (128 bytes of halves per row), R = roundup16(n) rows.
+__host__ __device__ inline int64_t umma_line_bytes16(int n, int* nkc) {
+    const int n4 = (n + 3) & ~3;
+    const int kc = (2 * n4 + 63) / 64;
+    if (nkc) *nkc = kc;
+    return (int64_t)kc * umma_rows(n, 1) * 128;
+}
+
 // Repack the column-major factors of every subdomain (k_factor.cu layout) into
 // the swizzled tile image, rounding to TF32.  One thread per output float.
 __global__ void repack_umma_kernel(const SubDesc* __restrict__ subs, const float* __restrict__ fac,
@@ -192,6 +220,71 @@ __global__ void repack_umma_kernel(const SubDesc* __restrict__ subs, const float
         v = D[(int64_t)q * 2 * S.nbp + part * S.nbp + p];
     }
     dst[dst_off[sub] / 4 + i] = __uint_as_float(to_tf32(v));  // dst_off in bytes
+}
+
+// Per-line power-of-two scale of the FP16 factor image: ascale[inva_off + j]
+// = 13 - floor(log2 max|Re, Im D_j|), so the largest entry of a line lands in
+// [2^13, 2^14) (FP16 holds up to 65504).  One block per (subdomain, line);
+// lines from nlines/2 on read the twisted factors.
+__global__ void line_scale_kernel(const SubDesc* __restrict__ subs, const float* __restrict__ fac,
+                                  const float* __restrict__ fac2, int* ascale) {
+    const SubDesc& S = subs[blockIdx.x];
+    const int j = blockIdx.y;
+    if (j >= S.nlines) return;
+    const float* src = (fac2 && j >= S.nlines / 2) ? fac2 : fac;
+    const float* D = src + S.fac_off + (int64_t)j * 2 * S.nbp * S.nbp;
+    const int n = S.nblk;
+    uint32_t mx = 0;
+    for (int64_t e = threadIdx.x; e < (int64_t)n * 2 * n; e += blockDim.x) {
+        const int q = (int)(e / (2 * n)), r = (int)(e % (2 * n));
+        const int part = r / n, p = r % n;
+        const float v = fabsf(D[(int64_t)q * 2 * S.nbp + part * S.nbp + p]);
+        mx = max(mx, __float_as_uint(v));  // non-negative floats order as their bits
+    }
+    mx = __reduce_max_sync(0xffffffffu, mx);
+    __shared__ uint32_t wm[32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) mx = max(mx, wm[w]);
+        mx = max(mx, wm[0]);
+        int sc = 0;
+        if (mx != 0 && mx < 0x7F800000u) {
+            const int e = (int)((mx >> 23) & 0xFF) - 127;  // floor(log2) of a normal float
+            sc = 13 - e;
+            sc = sc < -60 ? -60 : (sc > 60 ? 60 : sc);
+        }
+        ascale[S.inva_off + j] = sc;
+    }
+}
+
+// FP16 image of the factors for the twisted solve: [line][K chunk of 64][R rows x
+// 128 B], 128-byte swizzle, each line scaled by 2^ascale; one thread per half.
+__global__ void repack_f16_kernel(const SubDesc* __restrict__ subs, const float* __restrict__ fac,
+                                  const float* __restrict__ fac2, const int* __restrict__ ascale,
+                                  const int64_t* __restrict__ dst_off, __half* dst, int sub) {
+    const SubDesc& S = subs[sub];
+    int nkc;
+    const int64_t lb = umma_line_bytes16(S.nblk, &nkc) / 2;  // halves per line
+    const int R = umma_rows(S.nblk, 1);
+    const int64_t total = lb * S.nlines;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int j = (int)(i / lb);
+    const int64_t rem = i % lb;
+    const int kc = (int)(rem / (R * 64));
+    const int off = (int)(rem % (R * 64));
+    const int r = off / 64, pos = off % 64;  // row; half position within the 128-byte row
+    const int unit = (pos / 8) ^ (r % 8);
+    const int k = kc * 64 + unit * 8 + (pos % 8);
+    const int q = k >> 1, part = k & 1;
+    float v = 0.f;
+    if (r < S.nblk && q < S.nblk) {
+        const float* src = (fac2 && j >= S.nlines / 2) ? fac2 : fac;
+        const float* D = src + S.fac_off + (int64_t)j * 2 * S.nbp * S.nbp;
+        v = D[(int64_t)q * 2 * S.nbp + part * S.nbp + r] * pow2f(ascale[S.inva_off + j]);
+    }
+    dst[dst_off[sub] / 2 + i] = __float2half_rn(v);  // dst_off in bytes
 }
 
 __device__ __forceinline__ uint32_t cluster_rank() {
@@ -751,20 +844,33 @@ void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nb
 // one phase).  Every wait is bounded; on expiry the CTA raises the device
 // error word, each role leaves its loop, copies and MMAs are drained, the two
 // CTAs drain the middle copies between them, and TMEM is freed.
-constexpr int kTwP = 3;                        // producer / issuer pairs
-constexpr int kTwEpi = 8;                      // epilogue warps (two TMEM tiles)
-constexpr int kTwWarpProd = kTwEpi, kTwWarpIss = kTwWarpProd + kTwP;
-constexpr int kTwThreads = 32 * (kTwWarpIss + kTwP);
+// producer / issuer pairs: three for TF32 (288 KB of operand per line step),
+// two for FP16 (half the bytes)
+__host__ __device__ constexpr int tw_pairs(bool f16) { return f16 ? 2 : 3; }
+constexpr int kTwEpi = 8;  // epilogue warps (two TMEM tiles)
+constexpr int kTwWarpProd = kTwEpi;
+__host__ __device__ constexpr int tw_threads(bool f16) { return 32 * (kTwEpi + 2 * tw_pairs(f16)); }
 constexpr uint32_t kTwEpiThreads = 32 * kTwEpi;
 
-template <int PG>
-__global__ void __launch_bounds__(kTwThreads) solve_twist_kernel(
+// F16: operands in FP16 (kind::f16, K chunks of 64) with power-of-two
+// scales: each factor line by 2^ascale[line] (set when the image is built),
+// each right-hand-side column of B by a scale chosen every step from the
+// column's largest value (a reduction over the CTA, which holds every row),
+// so that both land in [2^13, 2^14); the FP32 accumulator is multiplied back
+// by the inverse powers of two.  FP16 keeps TF32's 10-bit mantissa, so entries
+// above ~2^-27 of their line's or column's largest carry the same rounding.
+template <int PG, bool F16>
+__global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
     const Task* __restrict__ tasks, const SubDesc* __restrict__ subs, int nrhs,
-    const float* __restrict__ afac, const int64_t* __restrict__ afac_off,
+    const void* __restrict__ afac_v, const int64_t* __restrict__ afac_off, const int* __restrict__ ascale,
     const cplx<float>* __restrict__ Pv, const cplx<float>* __restrict__ inva, cplx<float>* buf,
     int64_t rstride, int nstage, uint32_t ring_bytes, DevStatus ds) {
     constexpr int kN = 2 * PG;
     constexpr int kBChunkBytes = kN * 128;
+    constexpr int kKc = F16 ? 64 : 32;  // K values per 128-byte row of a chunk
+    constexpr int kTwP = tw_pairs(F16);
+    constexpr int kTwWarpIss = kTwWarpProd + kTwP;
+    const char* afac = reinterpret_cast<const char*>(afac_v);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t rank = cluster_rank();  // 0: top half, 1: bottom half
     const uint32_t peer = rank ^ 1u;
@@ -773,7 +879,7 @@ __global__ void __launch_bounds__(kTwThreads) solve_twist_kernel(
     const int n = S.nblk, nl = S.nlines, mid = nl / 2, nb = nl - 1 - mid;
     const int ntile = (n + 127) / 128;
     int nkc;
-    const int64_t line_bytes = umma_line_bytes(n, 1, &nkc);
+    const int64_t line_bytes = F16 ? umma_line_bytes16(n, &nkc) : umma_line_bytes(n, 1, &nkc);
     const int R = umma_rows(n, 1);
     const uint32_t stage_bytes = (uint32_t)R * 128;
     const int NS = nstage, NQ = NS / kTwP;
@@ -808,6 +914,7 @@ __global__ void __launch_bounds__(kTwThreads) solve_twist_kernel(
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* x_sent = reinterpret_cast<volatile int*>(tmem_slot + 2);  // this CTA sent its middle copy
     volatile int* x_peer = reinterpret_cast<volatile int*>(tmem_slot + 3);  // the peer sent its (exit)
+    uint32_t* s_red = tmem_slot + 4;  // [kTwEpi][PG] column maxima (F16 scales)
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr uint32_t kCols = 2 * kTwP * kN <= 32 ? 32 : 2 * kTwP * kN <= 64 ? 64 :
@@ -851,7 +958,7 @@ __global__ void __launch_bounds__(kTwThreads) solve_twist_kernel(
         // ====================================================== producers
         const int pq = warp - kTwWarpProd;
         if (lane == 0) {
-            const char* abase = reinterpret_cast<const char*>(afac) + afac_off[tk.sub];
+            const char* abase = afac + afac_off[tk.sub];
             int k = 0;
             for (int step = 0; step < nsteps && !*abort_flag; ++step) {
                 const int j = line_of(step);
@@ -875,7 +982,7 @@ __global__ void __launch_bounds__(kTwThreads) solve_twist_kernel(
         // ====================================================== MMA issuers
         const int q = warp - kTwWarpIss;
         if (lane == 0) {
-            constexpr uint32_t idesc = idesc_tf32(128, kN);
+            constexpr uint32_t idesc = F16 ? idesc_f16(128, kN) : idesc_tf32(128, kN);
             const uint64_t bdesc0 = desc_sw128(b0);
             int k = 0;
             for (int step = 0; step < nsteps && !*abort_flag; ++step) {
@@ -902,9 +1009,14 @@ __global__ void __launch_bounds__(kTwThreads) solve_twist_kernel(
                         const uint64_t adesc = desc_sw128(stage0 + s * stage_bytes + (uint32_t)t * kTileBytes);
                         const uint32_t dacc = tmem + (uint32_t)((t * kTwP + q) * kN);
 #pragma unroll
-                        for (int kk = 0; kk < 4; ++kk)
-                            umma_tf32(dacc, adesc + (uint64_t)(2 * kk), bdesc + (uint64_t)(2 * kk), idesc,
-                                      (first && kk == 0) ? 0u : 1u);
+                        for (int kk = 0; kk < 4; ++kk) {
+                            if constexpr (F16)
+                                umma_f16(dacc, adesc + (uint64_t)(2 * kk), bdesc + (uint64_t)(2 * kk), idesc,
+                                         (first && kk == 0) ? 0u : 1u);
+                            else
+                                umma_tf32(dacc, adesc + (uint64_t)(2 * kk), bdesc + (uint64_t)(2 * kk), idesc,
+                                          (first && kk == 0) ? 0u : 1u);
+                        }
                     }
                     first = false;
                     umma_commit(empty(s));
@@ -929,12 +1041,18 @@ __global__ void __launch_bounds__(kTwThreads) solve_twist_kernel(
         int ncol = nrhs - c0;
         if (ncol > PG) ncol = PG;
         const int k0 = 2 * p;
-        const int kcb = k0 / kChunkK, kkb = k0 % kChunkK;
+        const int kcb = k0 / kKc, kkb = k0 % kKc;
+        // byte offset of B[row][k0] (k0 and k0+1 adjacent in one 16-byte unit)
         auto boff = [&](int row) -> uint32_t {
-            const int chunk = (kkb / 4) ^ (row % 8);
-            return (uint32_t)(kcb * kBChunkBytes + row * 128 + chunk * 16 + (kkb % 4) * 4);
+            if constexpr (F16)
+                return (uint32_t)(kcb * kBChunkBytes + row * 128 + (((kkb / 8) ^ (row % 8)) * 16) + (kkb % 8) * 2);
+            else
+                return (uint32_t)(kcb * kBChunkBytes + row * 128 + (((kkb / 4) ^ (row % 8)) * 16) + (kkb % 4) * 4);
         };
         auto coup = [&](int face) -> cplx<float> { return rv ? pvp * ia[face] : mk<float>(0, 0); };
+        int sbv[PG];  // F16: exponent of the scale of each column of the current B
+#pragma unroll
+        for (int c = 0; c < PG; ++c) sbv[c] = 0;
         auto vload = [&](int j, cplx<float> (&dst)[PG]) {
 #pragma unroll
             for (int c = 0; c < PG; ++c)
@@ -950,7 +1068,38 @@ __global__ void __launch_bounds__(kTwThreads) solve_twist_kernel(
         // (writers' stores before the tensor cores' reads, TMEM loads before the
         // thread sync) one arrival on b_ready
         auto announce = [&](const cplx<float> (&v)[PG]) {
-            if (wr) {
+            if constexpr (F16) {
+                // column maxima over the CTA's rows -> scale exponents
+#pragma unroll
+                for (int c = 0; c < PG; ++c) {
+                    const float m = rv ? fmaxf(fabsf(v[c].re), fabsf(v[c].im)) : 0.f;
+                    const uint32_t wmx = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
+                    if (lane == 0) s_red[warp * PG + c] = wmx;
+                }
+                epi_sync(kTwEpiThreads);
+#pragma unroll
+                for (int c = 0; c < PG; ++c) {
+                    uint32_t mx = 0;
+#pragma unroll
+                    for (int w = 0; w < kTwEpi; ++w) mx = max(mx, s_red[w * PG + c]);
+                    int sc = 0;
+                    if (mx != 0 && mx < 0x7F800000u) {
+                        sc = 13 - ((int)((mx >> 23) & 0xFF) - 127);
+                        sc = sc < -100 ? -100 : (sc > 100 ? 100 : sc);
+                    }
+                    sbv[c] = sc;
+                }
+                if (wr) {
+                    __half* bh = reinterpret_cast<__half*>(bl);
+#pragma unroll
+                    for (int c = 0; c < PG; ++c) {
+                        const float s2 = pow2f(sbv[c]);
+                        const float re = v[c].re * s2, im = v[c].im * s2;
+                        *reinterpret_cast<__half2*>(bh + boff(2 * c) / 2) = __floats2half2_rn(re, -im);
+                        *reinterpret_cast<__half2*>(bh + boff(2 * c + 1) / 2) = __floats2half2_rn(im, re);
+                    }
+                }
+            } else if (wr) {
 #pragma unroll
                 for (int c = 0; c < PG; ++c) {
                     const float re = __uint_as_float(to_tf32(v[c].re)), im = __uint_as_float(to_tf32(v[c].im));
@@ -1033,8 +1182,17 @@ __global__ void __launch_bounds__(kTwThreads) solve_twist_kernel(
                     }
             }
             cplx<float> y[PG];
+            if constexpr (F16) {
+                const int sa = ascale[S.inva_off + j];
 #pragma unroll
-            for (int c = 0; c < PG; ++c) y[c] = mk<float>(acc[2 * c], acc[2 * c + 1]);
+                for (int c = 0; c < PG; ++c) {
+                    const float us = pow2f(-(sa + sbv[c]));
+                    y[c] = mk<float>(acc[2 * c] * us, acc[2 * c + 1] * us);
+                }
+            } else {
+#pragma unroll
+                for (int c = 0; c < PG; ++c) y[c] = mk<float>(acc[2 * c], acc[2 * c + 1]);
+            }
             bool last = step + 1 >= nsteps;
             if (rank == 0) {
                 if (step < mid) {  // y_j; next: b_{j+1} - a_{j+1} y_j (minus the bottom's c_mid z_{mid+1} at mid)
@@ -1128,17 +1286,22 @@ __global__ void __launch_bounds__(kTwThreads) solve_twist_kernel(
 
 // Shared-memory plan of a twisted launch: ns stages (kTwP sub-rings of at
 // least 2) of R*128 bytes plus the 256-row tail of the last one, B, the two
-// middle buffers, barriers and slots, alignment; 0 if it does not fit.
-static size_t twist_smem_plan(int PG, int nblk_max, int* ns_out, uint32_t* ring_out) {
+// middle buffers, barriers, slots and the column-maximum scratch, alignment;
+// 0 if it does not fit.
+static size_t twist_smem_plan(int PG, bool f16, int nblk_max, int* ns_out, uint32_t* ring_out) {
+    const int kTwP = tw_pairs(f16);
     int nkc = 0;
-    umma_line_bytes(nblk_max, 1, &nkc);
+    if (f16)
+        umma_line_bytes16(nblk_max, &nkc);
+    else
+        umma_line_bytes(nblk_max, 1, &nkc);
     const size_t sb = (size_t)umma_rows(nblk_max, 1) * 128;
     const size_t tail = 2 * (size_t)kTileBytes;  // the second tile's MMA reads 128 rows from +16 KB
     const size_t fixed = (size_t)nkc * 2 * PG * 128 + 2 * (size_t)umma_rows(nblk_max, 1) * PG * 8 + 1024 + 1024;
     const size_t budget = 227 * 1024;
     if (fixed + (2 * kTwP - 1) * sb + tail > budget) return 0;
     int ns = (int)((budget - fixed - tail) / sb) + 1;
-    if (ns > 32) ns = 32;
+    if (ns > 30) ns = 30;  // barriers, slots and the scratch within the 1 KB reserve
     ns -= ns % kTwP;
     *ns_out = ns;
     *ring_out = (uint32_t)((ns - 1) * sb + tail);
@@ -1148,22 +1311,40 @@ static size_t twist_smem_plan(int PG, int nblk_max, int* ns_out, uint32_t* ring_
 bool twist_supported(int nblk_max, int nlines_min) {
     int ns;
     uint32_t ring;
-    return nblk_max <= 256 && nlines_min >= 4 && twist_smem_plan(8, nblk_max, &ns, &ring) != 0;
+    return nblk_max <= 256 && nlines_min >= 4 && twist_smem_plan(8, false, nblk_max, &ns, &ring) != 0 &&
+           twist_smem_plan(8, true, nblk_max, &ns, &ring) != 0;
 }
 
-void launch_solve_twist(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
-                        const float* afac, const int64_t* afac_off, const cplx<float>* Pv,
-                        const cplx<float>* inva, cplx<float>* buf, int64_t rstride, DevStatus ds,
-                        cudaStream_t st) {
-    if (ntask == 0) return;
+int64_t twist_f16_factor_bytes(const SubDesc& S) { return umma_line_bytes16(S.nblk, nullptr) * S.nlines; }
+
+void launch_line_scales(const SubDesc* subs_d, int nsub, int max_lines, const float* fac, const float* fac2,
+                        int* ascale, cudaStream_t st) {
+    line_scale_kernel<<<dim3(nsub, max_lines), 256, 0, st>>>(subs_d, fac, fac2, ascale);
+}
+
+void launch_repack_f16(const SubDesc* subs_d, const std::vector<SubDesc>& subs_h, const float* fac,
+                       const float* fac2, const int* ascale, const int64_t* dst_off_d, void* dst,
+                       cudaStream_t st) {
+    for (size_t s = 0; s < subs_h.size(); ++s) {
+        const int64_t halves = umma_line_bytes16(subs_h[s].nblk, nullptr) / 2 * subs_h[s].nlines;
+        repack_f16_kernel<<<(unsigned)((halves + 255) / 256), 256, 0, st>>>(
+            subs_d, fac, fac2, ascale, dst_off_d, static_cast<__half*>(dst), (int)s);
+    }
+}
+
+template <bool F16>
+static void launch_twist_t(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
+                           const void* afac, const int64_t* afac_off, const int* ascale, const cplx<float>* Pv,
+                           const cplx<float>* inva, cplx<float>* buf, int64_t rstride, DevStatus ds,
+                           cudaStream_t st) {
     constexpr int PG = 8;
     int ns = 0;
     uint32_t ring = 0;
-    const size_t smem = twist_smem_plan(PG, nblk_max, &ns, &ring);
-    cudaFuncSetAttribute(solve_twist_kernel<PG>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = twist_smem_plan(PG, F16, nblk_max, &ns, &ring);
+    cudaFuncSetAttribute(solve_twist_kernel<PG, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ntask * 2, (nrhs + PG - 1) / PG, 1);
-    cfg.blockDim = dim3(kTwThreads, 1, 1);
+    cfg.blockDim = dim3(tw_threads(F16), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -1173,8 +1354,21 @@ void launch_solve_twist(const Task* tasks, int ntask, const SubDesc* subs, int n
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, solve_twist_kernel<PG>, tasks, subs, nrhs, afac, afac_off, Pv, inva, buf, rstride,
-                       ns, ring, ds);
+    cudaLaunchKernelEx(&cfg, solve_twist_kernel<PG, F16>, tasks, subs, nrhs, afac, afac_off, ascale, Pv, inva,
+                       buf, rstride, ns, ring, ds);
+}
+
+void launch_solve_twist(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
+                        const void* afac, const int64_t* afac_off, const int* ascale, bool f16,
+                        const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf, int64_t rstride,
+                        DevStatus ds, cudaStream_t st) {
+    if (ntask == 0) return;
+    if (f16)
+        launch_twist_t<true>(tasks, ntask, subs, nblk_max, nrhs, afac, afac_off, ascale, Pv, inva, buf, rstride,
+                             ds, st);
+    else
+        launch_twist_t<false>(tasks, ntask, subs, nblk_max, nrhs, afac, afac_off, ascale, Pv, inva, buf,
+                              rstride, ds, st);
 }
 
 }  // namespace helm

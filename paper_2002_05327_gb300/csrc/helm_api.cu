@@ -138,6 +138,8 @@ struct helm_ctx {
     bool umma_twist = false;           // tcgen05 solve in its twisted (two-ended) form
     bool f16 = false;                  // HELM_PREC_F16: FP16 operands in the twisted solve
     int* ascale_d = nullptr;           // per (subdomain, line) exponent of the FP16 factor scale
+    void* bsrc = nullptr;              // local sources b, same layout as buf; zero except where the
+                                       // gather writes (sweep-0 boxes, transfer strips)
     size_t inva_count = 0;             // entries of inva (nlines + 1 per subdomain)
     void* fac = nullptr;
     size_t fac_bytes = 0;
@@ -236,12 +238,15 @@ int ensure_buffers(helm_ctx* c, int nrhs) {
     if (nrhs <= c->cap_rhs && c->buf) return HELM_OK;
     if (c->buf) {
         cudaFree(c->buf);
-        c->dev_bytes -= (size_t)c->cap_rhs * c->buf_per_rhs * elem_size(c);
-        c->buf = nullptr;
+        cudaFree(c->bsrc);
+        c->dev_bytes -= 2 * (size_t)c->cap_rhs * c->buf_per_rhs * elem_size(c);
+        c->buf = c->bsrc = nullptr;
     }
     size_t bytes = (size_t)nrhs * c->buf_per_rhs * elem_size(c);
     CK(cudaMalloc(&c->buf, bytes));
-    c->dev_bytes += bytes;
+    CK(cudaMalloc(&c->bsrc, bytes));
+    CK(cudaMemsetAsync(c->bsrc, 0, bytes, c->stream));  // the gather writes only its fixed node set
+    c->dev_bytes += 2 * bytes;
     c->cap_rhs = nrhs;
     return HELM_OK;
 }
@@ -717,40 +722,42 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
         }
         if (c->prec == HELM_PREC_F64) {
             auto* buf = static_cast<cplx<double>*>(c->buf);
+            auto* bsrc = static_cast<cplx<double>*>(c->bsrc);
             {
                 ProfScope ps(c, HELM_K_GATHER, 1, gbytes);
                 launch_gather<double>(t, nt, c->max_win, c->subs_d, c->inc_d, c->P, c->m64,
-                                      c->an64, c->af64, c->tab64, b, nrhs, buf, rs, c->max_nw0,
+                                      c->an64, c->af64, c->tab64, b, nrhs, buf, bsrc, rs, c->max_nw0,
                                       c->max_lines12, c->stream);
             }
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
             launch_solve<double>(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
-                                 static_cast<const double*>(c->fac), c->Pv64, c->inva64, buf, rs,
+                                 static_cast<const double*>(c->fac), c->Pv64, c->inva64, buf, bsrc, rs,
                                  DevStatus{c->err_d, c->wait_polls}, c->stream);
         } else {
             auto* buf = static_cast<cplx<float>*>(c->buf);
+            auto* bsrc = static_cast<cplx<float>*>(c->bsrc);
             {
                 ProfScope ps(c, HELM_K_GATHER, 1, gbytes);
                 launch_gather<float>(t, nt, c->max_win, c->subs_d, c->inc_d, c->P, c->m32,
-                                     c->an32, c->af32, c->tab32, b, nrhs, buf, rs, c->max_nw0,
+                                     c->an32, c->af32, c->tab32, b, nrhs, buf, bsrc, rs, c->max_nw0,
                                      c->max_lines12, c->stream);
             }
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
             if (c->prec == HELM_PREC_TF32 && c->umma_twist)
                 launch_solve_twist(t, nt, c->subs_d, c->umma_nblk, nrhs, c->ufac, c->ufac_off, c->ascale_d,
-                                   c->f16, c->Pv32, c->inva32, buf, rs, DevStatus{c->err_d, c->wait_polls},
-                                   c->stream);
+                                   c->f16, c->Pv32, c->inva32, buf, bsrc, rs,
+                                   DevStatus{c->err_d, c->wait_polls}, c->stream);
             else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
                 launch_solve_umma(t, nt, c->subs_d, c->umma_nblk, nrhs, panel,
                                   static_cast<const float*>(c->ufac), c->ufac_off, c->Pv32,
-                                  c->inva32, buf, rs, DevStatus{c->err_d, c->wait_polls}, c->stream);
+                                  c->inva32, buf, bsrc, rs, DevStatus{c->err_d, c->wait_polls}, c->stream);
             else if (c->prec == HELM_PREC_TF32)
                 launch_solve_tc(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
-                                static_cast<const float*>(c->fac), c->Pv32, c->inva32, buf, rs,
+                                static_cast<const float*>(c->fac), c->Pv32, c->inva32, buf, bsrc, rs,
                                 DevStatus{c->err_d, c->wait_polls}, c->stream);
             else
                 launch_solve<float>(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
-                                    static_cast<const float*>(c->fac), c->Pv32, c->inva32, buf,
+                                    static_cast<const float*>(c->fac), c->Pv32, c->inva32, buf, bsrc,
                                     rs, DevStatus{c->err_d, c->wait_polls}, c->stream);
         }
     }
@@ -1224,23 +1231,27 @@ int helm_subdomain_solve(helm_ctx* c, int s, int nrhs, const void* R, void* U, i
     if (c->prec == HELM_PREC_F64)
         launch_solve<double>(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
                              static_cast<const double*>(c->fac), c->Pv64, c->inva64,
-                             static_cast<cplx<double>*>(wb), we, DevStatus{c->err_d, c->wait_polls}, c->stream);
+                             static_cast<cplx<double>*>(wb), static_cast<cplx<double>*>(wb), we,
+                             DevStatus{c->err_d, c->wait_polls}, c->stream);
     else if (c->prec == HELM_PREC_TF32 && c->umma_twist)
         launch_solve_twist(td, 1, c->subs_d, c->umma_nblk, nrhs, c->ufac, c->ufac_off, c->ascale_d, c->f16,
-                           c->Pv32, c->inva32, static_cast<cplx<float>*>(wb), we,
-                           DevStatus{c->err_d, c->wait_polls}, c->stream);
+                           c->Pv32, c->inva32, static_cast<cplx<float>*>(wb), static_cast<cplx<float>*>(wb),
+                           we, DevStatus{c->err_d, c->wait_polls}, c->stream);
     else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
         launch_solve_umma(td, 1, c->subs_d, c->umma_nblk, nrhs, panel,
                           static_cast<const float*>(c->ufac), c->ufac_off, c->Pv32, c->inva32,
-                          static_cast<cplx<float>*>(wb), we, DevStatus{c->err_d, c->wait_polls}, c->stream);
+                          static_cast<cplx<float>*>(wb), static_cast<cplx<float>*>(wb), we,
+                          DevStatus{c->err_d, c->wait_polls}, c->stream);
     else if (c->prec == HELM_PREC_TF32)
         launch_solve_tc(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
                         static_cast<const float*>(c->fac), c->Pv32, c->inva32,
-                        static_cast<cplx<float>*>(wb), we, DevStatus{c->err_d, c->wait_polls}, c->stream);
+                        static_cast<cplx<float>*>(wb), static_cast<cplx<float>*>(wb), we,
+                        DevStatus{c->err_d, c->wait_polls}, c->stream);
     else
         launch_solve<float>(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
                             static_cast<const float*>(c->fac), c->Pv32, c->inva32,
-                            static_cast<cplx<float>*>(wb), we, DevStatus{c->err_d, c->wait_polls}, c->stream);
+                            static_cast<cplx<float>*>(wb), static_cast<cplx<float>*>(wb), we,
+                            DevStatus{c->err_d, c->wait_polls}, c->stream);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->stream));
     if (c->prec == HELM_PREC_F64) {
@@ -1332,7 +1343,7 @@ void helm_destroy(helm_ctx* c) {
     void* ptrs[] = {c->ufac, c->ufac_off, c->subs_d, c->g_alpha, c->m64, c->m32, c->an64, c->af64, c->an32, c->af32,
                     c->Pv64, c->inva64, c->Pv32, c->inva32, c->tab64, c->tab32, c->box_of,
                     c->fac, c->err_d, c->tasks_d, c->inc_d, c->node_buf_d, c->buf, c->bvec,
-                    c->small_d, c->partial_d, c->scal_d, c->vptr_d, c->zptr_d, c->ascale_d};
+                    c->small_d, c->partial_d, c->scal_d, c->vptr_d, c->zptr_d, c->ascale_d, c->bsrc};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto* p : c->gm) cudaFree(p);

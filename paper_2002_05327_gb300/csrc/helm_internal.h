@@ -170,15 +170,18 @@ struct DevStatus {
     uint32_t polls;  // polls of each ordinary wait
 };
 
+// buf: y, then u of every solve (read by the transfers and the assembly);
+// bsrc: the local sources b the gather wrote (same layout), read by the solve.
 template <typename T>
 void launch_solve(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                   int panel, const T* fac, const cplx<T>* Pv, const cplx<T>* inva, cplx<T>* buf,
-                  int64_t buf_rhs_stride, DevStatus ds, cudaStream_t st);
+                  const cplx<T>* bsrc, int64_t buf_rhs_stride, DevStatus ds, cudaStream_t st);
 
 // Tensor-core (TF32 mma, FP32 accumulate) variant for complex64 factors.
 void launch_solve_tc(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                      int panel, const float* fac, const cplx<float>* Pv, const cplx<float>* inva,
-                     cplx<float>* buf, int64_t buf_rhs_stride, DevStatus ds, cudaStream_t st);
+                     cplx<float>* buf, const cplx<float>* bsrc, int64_t buf_rhs_stride, DevStatus ds,
+                     cudaStream_t st);
 void launch_round_tf32(float* x, int64_t count, cudaStream_t st);
 
 // tcgen05 (5th-generation tensor core) subdomain solve, k_solve_umma.cu.  The
@@ -204,19 +207,19 @@ void launch_repack_f16(const SubDesc* subs_d, const std::vector<SubDesc>& subs_h
                        cudaStream_t st);
 void launch_solve_twist(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
                         const void* afac, const int64_t* afac_off, const int* ascale, bool f16,
-                        const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf, int64_t rstride,
-                        DevStatus ds, cudaStream_t st);
+                        const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf,
+                        const cplx<float>* bsrc, int64_t rstride, DevStatus ds, cudaStream_t st);
 void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
                        int panel, const float* afac, const int64_t* afac_off,
                        const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf,
-                       int64_t rstride, DevStatus ds, cudaStream_t st);
+                       const cplx<float>* bsrc, int64_t rstride, DevStatus ds, cudaStream_t st);
 
 template <typename T>
 void launch_gather(const Task* tasks, int ntask, int64_t max_win, const SubDesc* subs,
                    const Incoming* inc, const DevProblem& P, const T* m, const cplx<T>* an,
                    const cplx<T>* af, const T* beta_tab, const cplx<double>* b, int nrhs,
-                   cplx<T>* buf, int64_t buf_rhs_stride, int max_line, int max_lines,
-                   cudaStream_t st);
+                   const cplx<T>* buf, cplx<T>* bsrc, int64_t buf_rhs_stride, int max_line, int max_lines,
+                   cudaStream_t st);  // reads the senders' solutions in buf, writes sources into bsrc
 
 template <typename T>
 void launch_assemble(const DevProblem& P, const SubDesc* subs, const int* box_of,

@@ -6,11 +6,11 @@
 // Reductions are deterministic: every block reduces a fixed contiguous chunk
 // with a fixed tree, and a second pass sums the block partials in order.
 //
-// The Gram-Schmidt kernels (multi-vector dots, combinations, norms) keep their
-// vectors in FP64 but do their arithmetic in float-float ("double-float"
-// pairs hi + lo) on the FP32 pipes: on this GPU the FP64 pipe issues about
-// one sixty-fourth of the FP32 rate, and the FP64 versions of these kernels
-// ran at ~87% of it.  A double is split exactly into its top 24 and next 24
+// The operator product and the Gram-Schmidt kernels (multi-vector dots,
+// combinations, norms) keep their vectors in FP64 but do their arithmetic in
+// float-float ("double-float" pairs hi + lo) on the FP32 pipes: on this GPU
+// the FP64 pipe issues about one sixty-fourth of the FP32 rate, and the FP64
+// versions of these kernels ran at ~87% of it.  A double is split exactly into its top 24 and next 24
 // mantissa bits with integer operations only (conversions from double would
 // use the FP64 pipe); products are formed exactly with FMA (TwoProd) and sums
 // are compensated (TwoSum), so a dot or combination carries ~48 significant
@@ -44,7 +44,19 @@ __device__ __forceinline__ ff split_d(double x) {
     if (es > 0) lo = __uint2float_rn((unsigned int)(m & 0x1FFFFFFFull)) * __uint_as_float((unsigned int)es << 23);
     return {hi, sign ? -lo : lo};
 }
-__device__ __forceinline__ double join_d(ff a) { return (double)a.hi + (double)a.lo; }
+// exact float -> double through the bits (normal floats; zero and values below
+// 2^-126 give 0): keeps the conversion off the FP64 pipe
+__device__ __forceinline__ double f2d(float f) {
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int e = (u >> 23) & 0xFF;
+    if (e == 0) return 0.0;
+    if (e == 0xFF) return (double)f;
+    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
+                                 ((unsigned long long)(e - 127 + 1023) << 52) |
+                                 ((unsigned long long)(u & 0x7FFFFFu) << 29);
+    return __longlong_as_double((long long)b);
+}
+__device__ __forceinline__ double join_d(ff a) { return f2d(a.hi) + f2d(a.lo); }
 
 // s += p with p's rounding error carried into the low word (Knuth's TwoSum)
 __device__ __forceinline__ void acc_add(ff& s, float p) {
@@ -105,7 +117,10 @@ void launch_scale_J(const DevProblem& P, const Win<double>& g, const cplx<double
 }
 
 // One thread per grid node: the stencil (FP64 complex reciprocals) is formed
-// once and applied to every right-hand side.
+// once, split into float-float, and applied to every right-hand side in
+// float-float arithmetic on the FP32 pipes (vectors stay FP64 in memory).
+// Outside the PML every alpha is 1, so the coefficients are real (their
+// imaginary parts are exact zeros) and each term needs two products, not four.
 __global__ void apply_A_kernel(DevProblem P, Win<double> w, const double* __restrict__ m,
                                const cplx<double>* __restrict__ b,
                                const cplx<double>* __restrict__ u, cplx<double>* __restrict__ r,
@@ -131,33 +146,45 @@ __global__ void apply_A_kernel(DevProblem P, Win<double> w, const double* __rest
         }
         stride *= P.N[a];
     }
-    // outside the PML every alpha is 1, so the coefficients are real (their
-    // imaginary parts are exact zeros) and each term needs two FMAs, not four
     bool real = st.diag.im == 0.0;
     for (int i = 0; i < np; ++i) real = real && co[i].im == 0.0;
-    if (real) {
-        for (int c = 0; c < nrhs; ++c) {
-            const cplx<double>* uc = u + (int64_t)c * Ng + k;
-            const cplx<double> u0 = uc[0];
-            double ar = st.diag.re * u0.re, ai = st.diag.re * u0.im;
-            for (int i = 0; i < np; ++i) {
-                const cplx<double> un = uc[off[i]];
-                ar = fma(co[i].re, un.re, ar);
-                ai = fma(co[i].re, un.im, ai);
-            }
-            cplx<double> out = mk<double>(-ar, -ai);
-            if (b) out = out + b[(int64_t)c * Ng + k];
-            r[(int64_t)c * Ng + k] = out;
-        }
-        return;
+    const ff dr = split_d(st.diag.re), di = split_d(st.diag.im);
+    ff cr[6], ci[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        cr[i] = i < np ? split_d(co[i].re) : ff{0.f, 0.f};
+        ci[i] = i < np ? split_d(co[i].im) : ff{0.f, 0.f};
     }
     for (int c = 0; c < nrhs; ++c) {
         const cplx<double>* uc = u + (int64_t)c * Ng + k;
-        cplx<double> Au = st.diag * uc[0];
-        for (int i = 0; i < np; ++i) Au = Au + co[i] * uc[off[i]];
-        cplx<double> out = cneg(Au);
-        if (b) out = out + b[(int64_t)c * Ng + k];
-        r[(int64_t)c * Ng + k] = out;
+        // -(A u) accumulated, then + b
+        ff ar = {0.f, 0.f}, ai = {0.f, 0.f};
+        if (b) {
+            const cplx<double> bv = b[(int64_t)c * Ng + k];
+            ar = split_d(bv.re);
+            ai = split_d(bv.im);
+        }
+        const cplx<double> u0 = uc[0];
+        const ff ur = split_d(u0.re), ui = split_d(u0.im);
+        acc_mul(ar, ff_neg(dr), ur);
+        acc_mul(ai, ff_neg(dr), ui);
+        if (!real) {
+            acc_mul(ar, di, ui);
+            acc_mul(ai, ff_neg(di), ur);
+        }
+#pragma unroll
+        for (int i = 0; i < 6; ++i) {
+            if (i >= np) break;
+            const cplx<double> un = uc[off[i]];
+            const ff nr = split_d(un.re), ni = split_d(un.im);
+            acc_mul(ar, ff_neg(cr[i]), nr);
+            acc_mul(ai, ff_neg(cr[i]), ni);
+            if (!real) {
+                acc_mul(ar, ci[i], ni);
+                acc_mul(ai, ff_neg(ci[i]), nr);
+            }
+        }
+        r[(int64_t)c * Ng + k] = mk<double>(join_d(ar), join_d(ai));
     }
 }
 
@@ -360,21 +387,28 @@ void launch_mdots(const cplx<double>* const* V, int nv, const cplx<double>* w, i
     dots_final_kernel<<<(count + 127) / 128, 128, 0, st>>>(partial, nblk, count, out);
 }
 
-// w[c] += sign * sum_i coef[i*nrhs+c] V_i[c], accumulated in float-float
+// w[c] += sign * sum_i coef[i*nrhs+c] V_i[c], accumulated in float-float; the
+// block's coefficients (one right-hand side per block row) are split once into
+// shared memory
 __global__ void mcombo_kernel(cplx<double>* w, const cplx<double>* const* __restrict__ V, int nv,
                               const cplx<double>* __restrict__ coef, int64_t n, int nrhs,
                               double sign) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    __shared__ ff scr[64], sci[64];
     const int c = blockIdx.y;
+    const float sg = sign < 0 ? -1.f : 1.f;  // sign is +-1
+    for (int i = threadIdx.x; i < nv; i += blockDim.x) {
+        const cplx<double> a = coef[i * nrhs + c];
+        const ff cr = split_d(a.re), ci = split_d(a.im);
+        scr[i] = {sg * cr.hi, sg * cr.lo};
+        sci[i] = {sg * ci.hi, sg * ci.lo};
+    }
+    __syncthreads();
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const cplx<double> w0 = w[(int64_t)c * n + k];
     ff ar = split_d(w0.re), ai = split_d(w0.im);
-    const float sg = sign < 0 ? -1.f : 1.f;  // sign is +-1
     for (int i = 0; i < nv; ++i) {
-        const cplx<double> a = coef[i * nrhs + c];
-        ff cr = split_d(a.re), ci = split_d(a.im);
-        cr = {sg * cr.hi, sg * cr.lo};
-        ci = {sg * ci.hi, sg * ci.lo};
+        const ff cr = scr[i], ci = sci[i];
         const cplx<double> v = V[i][(int64_t)c * n + k];
         const ff vr = split_d(v.re), vi = split_d(v.im);
         // (cr + i ci)(vr + i vi)

@@ -79,7 +79,7 @@ static cudaError_t run(const NoAllocArgs& a, void* scratch) {
     noalloc_write_task<<<1, 1, 0, a.stream>>>(task, Task{0, a.sub, 0, 0, 0});
     noalloc_pack<T><<<blocks, 256, 0, a.stream>>>(a.R, wb, count);
     launch_solve<T>(task, 1, a.subs, a.nbp_max, a.nrhs, a.panel, static_cast<const T*>(a.fac),
-                    static_cast<const cplx<T>*>(a.Pv), static_cast<const cplx<T>*>(a.inva), wb,
+                    static_cast<const cplx<T>*>(a.Pv), static_cast<const cplx<T>*>(a.inva), wb, wb,
                     a.win_elems, DevStatus{a.err, a.polls}, a.stream);
     noalloc_unpack<T><<<blocks, 256, 0, a.stream>>>(wb, a.U, count);
     return cudaGetLastError();

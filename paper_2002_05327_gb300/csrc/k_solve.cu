@@ -112,8 +112,9 @@ __global__ void __launch_bounds__(1024) solve_kernel(const Task* __restrict__ ta
                                                      const T* __restrict__ fac,
                                                      const cplx<T>* __restrict__ Pv,
                                                      const cplx<T>* __restrict__ inva,
-                                                     cplx<T>* buf, int64_t rstride, SolveGeom G,
-                                                     int nbp_max, DevStatus ds) {
+                                                     cplx<T>* buf, const cplx<T>* __restrict__ bsrc,
+                                                     int64_t rstride, SolveGeom G, int nbp_max,
+                                                     DevStatus ds) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     const Task tk = tasks[blockIdx.x];
     const SubDesc& S = subs[tk.sub];
@@ -172,7 +173,8 @@ __global__ void __launch_bounds__(1024) solve_kernel(const Task* __restrict__ ta
     if (ncol > PG) ncol = PG;
     const cplx<T>* pv = Pv + S.coup_off;
     const cplx<T>* ia = inva + S.inva_off;
-    cplx<T>* V = buf + tk.buf_off;
+    cplx<T>* V = buf + tk.buf_off;           // y, then u
+    const cplx<T>* B = bsrc + tk.buf_off;    // the local source b
     int prow[RPT];
     bool row[RPT];
     cplx<T> pvp[RPT];
@@ -192,7 +194,7 @@ __global__ void __launch_bounds__(1024) solve_kernel(const Task* __restrict__ ta
 #pragma unroll
         for (int c = 0; c < PG; ++c) {
             prev[r][c] = mk<T>(0, 0);
-            pre[r][c] = (row[r] && c < ncol) ? V[vidx(c, 0, prow[r])] : mk<T>(0, 0);
+            pre[r][c] = (row[r] && c < ncol) ? B[vidx(c, 0, prow[r])] : mk<T>(0, 0);
         }
 
     int ci = 0;
@@ -246,7 +248,7 @@ __global__ void __launch_bounds__(1024) solve_kernel(const Task* __restrict__ ta
         for (int r = 0; r < RPT; ++r)
 #pragma unroll
             for (int c = 0; c < PG; ++c)
-                pre[r][c] = (row[r] && c < ncol && j + 1 < nl) ? V[vidx(c, j + 1, prow[r])]
+                pre[r][c] = (row[r] && c < ncol && j + 1 < nl) ? B[vidx(c, j + 1, prow[r])]
                                                                 : mk<T>(0, 0);
         line_gemv(panel);
 #pragma unroll
@@ -304,44 +306,44 @@ static SolveGeom geom_for(int nbp_max, size_t esize, int PG, int RPT, size_t* sm
 template <typename T, int PG, int RPT>
 static void launch_cfg(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                        const T* fac, const cplx<T>* Pv, const cplx<T>* inva, cplx<T>* buf,
-                       int64_t rstride, DevStatus ds, cudaStream_t st) {
+                       const cplx<T>* bsrc, int64_t rstride, DevStatus ds, cudaStream_t st) {
     size_t smem = 0;
     SolveGeom g = geom_for(nbp_max, sizeof(T), PG, RPT, &smem);
     cudaFuncSetAttribute(solve_kernel<T, PG, RPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)smem);
     dim3 grid(ntask, (nrhs + PG - 1) / PG);
     solve_kernel<T, PG, RPT><<<grid, g.ncons + 32, smem, st>>>(tasks, subs, nrhs, fac, Pv, inva,
-                                                               buf, rstride, g, nbp_max, ds);
+                                                               buf, bsrc, rstride, g, nbp_max, ds);
 }
 
 template <typename T, int PG>
 static void launch_pg(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                       const T* fac, const cplx<T>* Pv, const cplx<T>* inva, cplx<T>* buf,
-                      int64_t rstride, DevStatus ds, cudaStream_t st) {
+                      const cplx<T>* bsrc, int64_t rstride, DevStatus ds, cudaStream_t st) {
     if (nbp_max <= 960)
-        launch_cfg<T, PG, 1>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, ds, st);
+        launch_cfg<T, PG, 1>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, bsrc, rstride, ds, st);
     else
-        launch_cfg<T, PG, 2>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, ds, st);
+        launch_cfg<T, PG, 2>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, bsrc, rstride, ds, st);
 }
 
 template <typename T>
 void launch_solve(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                   int panel, const T* fac, const cplx<T>* Pv, const cplx<T>* inva, cplx<T>* buf,
-                  int64_t rstride, DevStatus ds, cudaStream_t st) {
+                  const cplx<T>* bsrc, int64_t rstride, DevStatus ds, cudaStream_t st) {
     if (ntask == 0) return;
     switch (panel) {
-        case 1: launch_pg<T, 1>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, ds, st); break;
-        case 2: launch_pg<T, 2>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, ds, st); break;
-        case 4: launch_pg<T, 4>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, ds, st); break;
-        default: launch_pg<T, 8>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, ds, st); break;
+        case 1: launch_pg<T, 1>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, bsrc, rstride, ds, st); break;
+        case 2: launch_pg<T, 2>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, bsrc, rstride, ds, st); break;
+        case 4: launch_pg<T, 4>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, bsrc, rstride, ds, st); break;
+        default: launch_pg<T, 8>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, bsrc, rstride, ds, st); break;
     }
 }
 
 template void launch_solve<float>(const Task*, int, const SubDesc*, int, int, int, const float*,
-                                  const cplx<float>*, const cplx<float>*, cplx<float>*, int64_t,
-                                  DevStatus, cudaStream_t);
+                                  const cplx<float>*, const cplx<float>*, cplx<float>*,
+                                  const cplx<float>*, int64_t, DevStatus, cudaStream_t);
 template void launch_solve<double>(const Task*, int, const SubDesc*, int, int, int,
                                    const double*, const cplx<double>*, const cplx<double>*,
-                                   cplx<double>*, int64_t, DevStatus, cudaStream_t);
+                                   cplx<double>*, const cplx<double>*, int64_t, DevStatus, cudaStream_t);
 
 }  // namespace helm

@@ -107,7 +107,9 @@ __global__ void __launch_bounds__(1024) solve_tc_kernel(const Task* __restrict__
                                                         int nrhs, const float* __restrict__ fac,
                                                         const cplx<float>* __restrict__ Pv,
                                                         const cplx<float>* __restrict__ inva,
-                                                        cplx<float>* buf, int64_t rstride,
+                                                        cplx<float>* buf,
+                                                        const cplx<float>* __restrict__ bsrc,
+                                                        int64_t rstride,
                                                         TcGeom G, int nbp_max, DevStatus ds) {
     constexpr int PG = 4 * NT;
     constexpr int BS = 8 * NT + (NT > 1 ? 8 : 0);  // floats per B row
@@ -173,7 +175,8 @@ __global__ void __launch_bounds__(1024) solve_tc_kernel(const Task* __restrict__
     const int c0 = blockIdx.y * PG;
     const cplx<float>* pv = Pv + S.coup_off;
     const cplx<float>* ia = inva + S.inva_off;
-    cplx<float>* V = buf + tk.buf_off;
+    cplx<float>* V = buf + tk.buf_off;          // y, then u
+    const cplx<float>* B = bsrc + tk.buf_off;   // the local source b
 
     // owned outputs: rows row[i][h] = 16*(warp*MTW+i) + g + 8h, columns c = 4*nt + t
     int row[MTW][2];
@@ -211,7 +214,7 @@ __global__ void __launch_bounds__(1024) solve_tc_kernel(const Task* __restrict__
         for (int h = 0; h < 2; ++h)
 #pragma unroll
             for (int nt = 0; nt < NT; ++nt) {
-                cplx<float> b = (rv[i][h] && cv[nt]) ? V[vidx(nt, 0, row[i][h])] : mk<float>(0, 0);
+                cplx<float> b = (rv[i][h] && cv[nt]) ? B[vidx(nt, 0, row[i][h])] : mk<float>(0, 0);
                 prev[i][h][nt] = mk<float>(0, 0);
                 if (row[i][h] < n4) put_b(0, row[i][h], nt, b);
             }
@@ -232,7 +235,7 @@ __global__ void __launch_bounds__(1024) solve_tc_kernel(const Task* __restrict__
                 for (int nt = 0; nt < NT; ++nt) {
                     const int jj = fwd ? j + 1 : j;
                     const bool ld = rv[i][h] && cv[nt] && jj < nl;
-                    pre[i][h][nt] = ld ? V[vidx(nt, jj, row[i][h])] : mk<float>(0, 0);
+                    pre[i][h][nt] = ld ? (fwd ? B : V)[vidx(nt, jj, row[i][h])] : mk<float>(0, 0);
                 }
 #pragma unroll
         for (int i = 0; i < MTW; ++i)
@@ -329,7 +332,8 @@ static TcGeom tc_geom(int nbp_max, int kpad, int mtiles, int MTW, int NT, size_t
 template <int NT, int MTW>
 static void launch_tc(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                       const float* fac, const cplx<float>* Pv, const cplx<float>* inva,
-                      cplx<float>* buf, int64_t rstride, DevStatus ds, cudaStream_t st) {
+                      cplx<float>* buf, const cplx<float>* bsrc, int64_t rstride, DevStatus ds,
+                      cudaStream_t st) {
     const int mtiles = (nbp_max + 15) / 16;
     const int kpad = ((nbp_max + 3) & ~3);
     size_t smem = 0;
@@ -338,19 +342,20 @@ static void launch_tc(const Task* tasks, int ntask, const SubDesc* subs, int nbp
                          (int)smem);
     dim3 grid(ntask, (nrhs + 4 * NT - 1) / (4 * NT));
     solve_tc_kernel<NT, MTW><<<grid, 32 * G.ncw + 32, smem, st>>>(tasks, subs, nrhs, fac, Pv,
-                                                                  inva, buf, rstride, G, nbp_max,
+                                                                  inva, buf, bsrc, rstride, G, nbp_max,
                                                                   ds);
 }
 
 void launch_solve_tc(const Task* tasks, int ntask, const SubDesc* subs, int nbp_max, int nrhs,
                      int panel, const float* fac, const cplx<float>* Pv, const cplx<float>* inva,
-                     cplx<float>* buf, int64_t rstride, DevStatus ds, cudaStream_t st) {
+                     cplx<float>* buf, const cplx<float>* bsrc, int64_t rstride, DevStatus ds,
+                     cudaStream_t st) {
     if (ntask == 0) return;
     const int mtiles = (nbp_max + 15) / 16;
     const int MTW = mtiles <= 31 ? 1 : mtiles <= 62 ? 2 : 4;
     const bool wide = panel >= 8;
 #define HELM_TC(NT_, MTW_) \
-    launch_tc<NT_, MTW_>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, rstride, ds, st)
+    launch_tc<NT_, MTW_>(tasks, ntask, subs, nbp_max, nrhs, fac, Pv, inva, buf, bsrc, rstride, ds, st)
     if (MTW == 1) {
         if (panel >= 16) HELM_TC(4, 1); else if (wide) HELM_TC(2, 1); else HELM_TC(1, 1);
     } else if (MTW == 2) {

@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kThreads) solve_umma_kernel(
     const Task* __restrict__ tasks, const SubDesc* __restrict__ subs, int nrhs, int CR,
     const float* __restrict__ afac, const int64_t* __restrict__ afac_off,
     const cplx<float>* __restrict__ Pv, const cplx<float>* __restrict__ inva, cplx<float>* buf,
-    int64_t rstride, int nstage, uint32_t ring_bytes, DevStatus ds) {
+    const cplx<float>* __restrict__ bsrc, int64_t rstride, int nstage, uint32_t ring_bytes, DevStatus ds) {
     constexpr int kN = 2 * PG;              // real columns
     constexpr int kBChunkBytes = kN * 128;  // B rows of one K chunk
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -621,17 +621,19 @@ __global__ void __launch_bounds__(kThreads) solve_umma_kernel(
             if (step < nl) return step + 1 < nl ? step + 1 : -1;
             return 2 * nl - 2 - step;
         };
+        const cplx<float>* Bsrc = bsrc + tk.buf_off;  // the local source b
         auto load_operand = [&](int step, cplx<float> (&dst)[PG]) {
             const int jj = operand_line(step);
+            const cplx<float>* src = step < nl ? Bsrc : V;  // b_{j+1} forward, y_j backward
 #pragma unroll
             for (int c = 0; c < PG; ++c)
-                dst[c] = (rv && c < ncol && jj >= 0) ? V[(int64_t)(c0 + c) * rstride + (int64_t)jj * n + p]
+                dst[c] = (rv && c < ncol && jj >= 0) ? src[(int64_t)(c0 + c) * rstride + (int64_t)jj * n + p]
                                                      : mk<float>(0, 0);
         };
         cplx<float> pre[PG], pre_next[PG], outv[PG], nbv[PG];
 #pragma unroll
         for (int c = 0; c < PG; ++c)
-            nbv[c] = (rv && c < ncol) ? V[(int64_t)(c0 + c) * rstride + p] : mk<float>(0, 0);
+            nbv[c] = (rv && c < ncol) ? Bsrc[(int64_t)(c0 + c) * rstride + p] : mk<float>(0, 0);
         load_operand(0, pre);
         announce(0, nbv);
         for (int step = 0; step < nsteps; ++step) {
@@ -770,8 +772,8 @@ static size_t umma_smem_plan(int PG, int CR, int nblk_max, int* ns_out, uint32_t
 template <int PG>
 static void launch_pg(const Task* tasks, int ntask, const SubDesc* subs, int CR, int nblk_max,
                       int nrhs, const float* afac, const int64_t* afac_off, const cplx<float>* Pv,
-                      const cplx<float>* inva, cplx<float>* buf, int64_t rstride, DevStatus ds,
-                      cudaStream_t st) {
+                      const cplx<float>* inva, cplx<float>* buf, const cplx<float>* bsrc, int64_t rstride,
+                      DevStatus ds, cudaStream_t st) {
     int ns = 0;
     uint32_t ring_bytes = 0;
     const size_t smem = umma_smem_plan(PG, CR, nblk_max, &ns, &ring_bytes);
@@ -789,7 +791,7 @@ static void launch_pg(const Task* tasks, int ntask, const SubDesc* subs, int CR,
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, solve_umma_kernel<PG>, tasks, subs, nrhs, CR, afac, afac_off, Pv, inva,
-                       buf, rstride, ns, ring_bytes, ds);
+                       buf, bsrc, rstride, ns, ring_bytes, ds);
 }
 
 bool umma_supported(int nblk_max) {
@@ -801,7 +803,7 @@ bool umma_supported(int nblk_max) {
 void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
                        int panel, const float* afac, const int64_t* afac_off,
                        const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf,
-                       int64_t rstride, DevStatus ds, cudaStream_t st) {
+                       const cplx<float>* bsrc, int64_t rstride, DevStatus ds, cudaStream_t st) {
     if (ntask == 0) return;
     const int CR = umma_tiles(nblk_max);  // cluster of ceil(n / 128) CTAs, rows split evenly
     int ns;
@@ -810,7 +812,7 @@ void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nb
     int pg = panel >= 32 ? 32 : panel >= 16 ? 16 : 8;
     while (pg > 8 && umma_smem_plan(pg, CR, nblk_max, &ns, &ring) == 0) pg /= 2;
 #define HELM_UMMA(PG_) \
-    launch_pg<PG_>(tasks, ntask, subs, CR, nblk_max, nrhs, afac, afac_off, Pv, inva, buf, rstride, ds, st)
+    launch_pg<PG_>(tasks, ntask, subs, CR, nblk_max, nrhs, afac, afac_off, Pv, inva, buf, bsrc, rstride, ds, st)
     if (pg == 32) HELM_UMMA(32); else if (pg == 16) HELM_UMMA(16); else HELM_UMMA(8);
 #undef HELM_UMMA
 }
@@ -864,7 +866,7 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
     const Task* __restrict__ tasks, const SubDesc* __restrict__ subs, int nrhs,
     const void* __restrict__ afac_v, const int64_t* __restrict__ afac_off, const int* __restrict__ ascale,
     const cplx<float>* __restrict__ Pv, const cplx<float>* __restrict__ inva, cplx<float>* buf,
-    int64_t rstride, int nstage, uint32_t ring_bytes, DevStatus ds) {
+    const cplx<float>* __restrict__ bsrc, int64_t rstride, int nstage, uint32_t ring_bytes, DevStatus ds) {
     constexpr int kN = 2 * PG;
     constexpr int kBChunkBytes = kN * 128;
     constexpr int kKc = F16 ? 64 : 32;  // K values per 128-byte row of a chunk
@@ -1053,10 +1055,13 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
         int sbv[PG];  // F16: exponent of the scale of each column of the current B
 #pragma unroll
         for (int c = 0; c < PG; ++c) sbv[c] = 0;
-        auto vload = [&](int j, cplx<float> (&dst)[PG]) {
+        const cplx<float>* Bsrc = bsrc + tk.buf_off;  // the local source b
+        // line j of the source (b) or of this solve's own output (y, z)
+        auto vload = [&](int j, bool src_b, cplx<float> (&dst)[PG]) {
+            const cplx<float>* src = src_b ? Bsrc : V;
 #pragma unroll
             for (int c = 0; c < PG; ++c)
-                dst[c] = (rv && c < ncol && j >= 0) ? V[(int64_t)(c0 + c) * rstride + (int64_t)j * n + p]
+                dst[c] = (rv && c < ncol && j >= 0) ? src[(int64_t)(c0 + c) * rstride + (int64_t)j * n + p]
                                                     : mk<float>(0, 0);
         };
         auto vstore = [&](int j, const cplx<float> (&v)[PG]) {
@@ -1142,15 +1147,17 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
             if (st < nb) return (nl - 2 - st > mid) ? nl - 2 - st : -1;
             return mid + 1 + (st - nb);
         };
+        // the forward steps' operand is the source b, the backward steps' their y / z
+        auto pre_is_b = [&](int st) -> bool { return rank == 0 ? st < mid : st < nb; };
         cplx<float> pre[PG], pre_next[PG], outv[PG], nbv[PG], xv[PG];
         bool ok = true;
         // first B: b_0 (top) or b_{nl-1} (bottom)
-        vload(rank == 0 ? 0 : nl - 1, nbv);
-        vload(pre_line(0), pre);
+        vload(rank == 0 ? 0 : nl - 1, true, nbv);
+        vload(pre_line(0), pre_is_b(0), pre);
         announce(nbv);
         for (int step = 0; step < nsteps; ++step) {
             const int j = line_of(step);
-            vload(pre_line(step + 1), pre_next);
+            vload(pre_line(step + 1), pre_is_b(step + 1), pre_next);
             bool bad = *abort_flag || !mb_wait(acc_full, (uint32_t)(step & 1), ds.polls);
             if (epi_any(bad, kTwEpiThreads)) {
                 ok = false;
@@ -1335,8 +1342,8 @@ void launch_repack_f16(const SubDesc* subs_d, const std::vector<SubDesc>& subs_h
 template <bool F16>
 static void launch_twist_t(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
                            const void* afac, const int64_t* afac_off, const int* ascale, const cplx<float>* Pv,
-                           const cplx<float>* inva, cplx<float>* buf, int64_t rstride, DevStatus ds,
-                           cudaStream_t st) {
+                           const cplx<float>* inva, cplx<float>* buf, const cplx<float>* bsrc, int64_t rstride,
+                           DevStatus ds, cudaStream_t st) {
     constexpr int PG = 8;
     int ns = 0;
     uint32_t ring = 0;
@@ -1355,19 +1362,19 @@ static void launch_twist_t(const Task* tasks, int ntask, const SubDesc* subs, in
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     cudaLaunchKernelEx(&cfg, solve_twist_kernel<PG, F16>, tasks, subs, nrhs, afac, afac_off, ascale, Pv, inva,
-                       buf, rstride, ns, ring, ds);
+                       buf, bsrc, rstride, ns, ring, ds);
 }
 
 void launch_solve_twist(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
                         const void* afac, const int64_t* afac_off, const int* ascale, bool f16,
-                        const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf, int64_t rstride,
-                        DevStatus ds, cudaStream_t st) {
+                        const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf,
+                        const cplx<float>* bsrc, int64_t rstride, DevStatus ds, cudaStream_t st) {
     if (ntask == 0) return;
     if (f16)
-        launch_twist_t<true>(tasks, ntask, subs, nblk_max, nrhs, afac, afac_off, ascale, Pv, inva, buf, rstride,
-                             ds, st);
+        launch_twist_t<true>(tasks, ntask, subs, nblk_max, nrhs, afac, afac_off, ascale, Pv, inva, buf, bsrc,
+                             rstride, ds, st);
     else
-        launch_twist_t<false>(tasks, ntask, subs, nblk_max, nrhs, afac, afac_off, ascale, Pv, inva, buf,
+        launch_twist_t<false>(tasks, ntask, subs, nblk_max, nrhs, afac, afac_off, ascale, Pv, inva, buf, bsrc,
                               rstride, ds, st);
 }
 

@@ -43,7 +43,8 @@ __global__ void __launch_bounds__(128) gather_kernel(const Task* __restrict__ ta
                                                      const cplx<T>* __restrict__ af,
                                                      const T* __restrict__ tab,
                                                      const cplx<double>* __restrict__ b, int nrhs,
-                                                     cplx<T>* buf, int64_t rstride) {
+                                                     const cplx<T>* __restrict__ buf, cplx<T>* bsrc,
+                                                     int64_t rstride) {
     struct InS {
         int dir[3];
         int blo[3], bhi[3];  // sender box
@@ -95,6 +96,9 @@ __global__ void __launch_bounds__(128) gather_kernel(const Task* __restrict__ ta
     }
     for (int i = threadIdx.x; i <= P.d; i += blockDim.x) stab[i] = tab[i];
     __syncthreads();
+    // only the sweep-0 box and the strips of the incoming transfers are ever
+    // written (the rest of bsrc stays zero): a line no strip meets has nothing
+    if (tk.sweep != 0 && nsel == 0) return;
     const int x0 = xspan * blockDim.x + threadIdx.x;
     if (x0 >= S.nw[0]) return;
     g[0] = S.lo[0] + x0;
@@ -104,8 +108,8 @@ __global__ void __launch_bounds__(128) gather_kernel(const Task* __restrict__ ta
     const int64_t gidx = ((int64_t)g[2] * P.N[1] + g[1]) * P.N[0] + g[0];
     const int c0 = blockIdx.z * kRG;
     const int nc = min(kRG, nrhs - c0);
-    cplx<T>* __restrict__ out = buf + tk.buf_off + k + (int64_t)c0 * rstride;
-    const cplx<T>* __restrict__ src = buf;  // sender windows: disjoint from this window
+    cplx<T>* __restrict__ out = bsrc + tk.buf_off + k + (int64_t)c0 * rstride;
+    const cplx<T>* __restrict__ src = buf;  // sender solutions
 
     bool inbox = tk.sweep == 0;
     for (int a = 0; a < ndim; ++a) inbox &= (g[a] >= S.box_lo[a]) && (g[a] < S.box_hi[a]);
@@ -115,6 +119,7 @@ __global__ void __launch_bounds__(128) gather_kernel(const Task* __restrict__ ta
         val[c] = (inbox && c < nc) ? ccast<T>(b[(int64_t)(c0 + c) * Ng + gidx]) : mk<T>(0, 0);
 
     bool have_st = false;
+    bool touched = inbox;  // the node belongs to the fixed set of written nodes
     cplx<T> coef[7];
     const int npt = 1 + 2 * ndim;
     const int ns = nsel;
@@ -125,6 +130,7 @@ __global__ void __launch_bounds__(128) gather_kernel(const Task* __restrict__ ta
         if (dd0 > 0) in = (g[0] >= R.bhi[0]) && (g[0] <= R.bhi[0] + P.d);
         if (dd0 < 0) in = (g[0] < R.blo[0]) && (g[0] >= R.blo[0] - 1 - P.d);
         if (!in) continue;
+        touched = true;
         if (!have_st) {
             Win<T> w;
             for (int a = 0; a < 3; ++a) {
@@ -169,6 +175,7 @@ __global__ void __launch_bounds__(128) gather_kernel(const Task* __restrict__ ta
                 if (c < nc) val[c] = val[c] - cw * sp[(int64_t)c * rstride];
         }
     }
+    if (!touched) return;
 #pragma unroll
     for (int c = 0; c < kRG; ++c)
         if (c < nc) out[(int64_t)c * rstride] = val[c];
@@ -178,26 +185,32 @@ template <typename T>
 void launch_gather(const Task* tasks, int ntask, int64_t max_win, const SubDesc* subs,
                    const Incoming* inc, const DevProblem& P, const T* m, const cplx<T>* an,
                    const cplx<T>* af, const T* beta_tab, const cplx<double>* b, int nrhs,
-                   cplx<T>* buf, int64_t rstride, int max_line, int max_lines, cudaStream_t st) {
+                   const cplx<T>* buf, cplx<T>* bsrc, int64_t rstride, int max_line, int max_lines,
+                   cudaStream_t st) {
     if (ntask == 0) return;
     const int nt = 128;
     const int spans = (max_line + nt - 1) / nt;
     dim3 grid((unsigned)(spans * max_lines), ntask, (nrhs + kRG - 1) / kRG);
-    gather_kernel<T><<<grid, nt, 0, st>>>(tasks, subs, inc, P, m, an, af, beta_tab, b, nrhs, buf,
+    gather_kernel<T><<<grid, nt, 0, st>>>(tasks, subs, inc, P, m, an, af, beta_tab, b, nrhs, buf, bsrc,
                                            rstride);
 }
 
 // ----------------------------------------------------------------------------- assembly
+constexpr int kAG = 8;  // right-hand sides per assembly thread
+
 template <typename T>
 __global__ void assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs,
                                 const int* __restrict__ box_of, const int64_t* __restrict__ node_buf,
                                 int nsweeps, const T* __restrict__ tab,
-                                const cplx<T>* __restrict__ buf, int64_t rstride,
+                                const cplx<T>* __restrict__ buf, int64_t rstride, int nrhs,
                                 cplx<double>* U) {
+    // one thread per (global node, group of kAG right-hand sides): the boxes
+    // whose cutoff reaches the node and their weights are found once, then
+    // applied to the group with independent loads
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = blockIdx.y;
     if (k >= Ng) return;
+    const int c0 = blockIdx.y * kAG;
     const int ndim = P.ndim;
     int g[3];
     g[0] = (int)(k % P.N[0]);
@@ -217,15 +230,12 @@ __global__ void assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs,
         const int i0 = box_of[off + g[a]];
         off += P.N[a];
         cb[a][0] = i0;
+        int stride = 1;
+        for (int b2 = 0; b2 < a; ++b2) stride *= P.nb[b2];
         // neighbour above: its lower cutoff at the m-th node below its face
         if (i0 + 1 < P.nb[a]) {
-            int lo1 = -1;
-            // find box lo of i0+1 via a subdomain that has it
-            int s = 0, stride = 1;
-            for (int b2 = 0; b2 < a; ++b2) stride *= P.nb[b2];
-            s = (i0 + 1) * stride;
-            lo1 = subs[s].box_lo[a];
-            int mm = lo1 - 1 - g[a];
+            const int lo1 = subs[(i0 + 1) * stride].box_lo[a];
+            const int mm = lo1 - 1 - g[a];
             if (mm < P.d) {
                 cb[a][cn[a]] = i0 + 1;
                 cw[a][cn[a]] = tab[mm];
@@ -233,10 +243,8 @@ __global__ void assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs,
             }
         }
         if (i0 > 0) {
-            int stride = 1;
-            for (int b2 = 0; b2 < a; ++b2) stride *= P.nb[b2];
-            int hi0 = subs[(i0 - 1) * stride].box_hi[a];
-            int mm = g[a] - hi0;
+            const int hi0 = subs[(i0 - 1) * stride].box_hi[a];
+            const int mm = g[a] - hi0;
             if (mm < P.d) {
                 cb[a][cn[a]] = i0 - 1;
                 cw[a][cn[a]] = tab[mm];
@@ -244,25 +252,63 @@ __global__ void assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs,
             }
         }
     }
-    double sr = 0, si = 0;
-    for (int i0 = 0; i0 < cn[0]; ++i0)
-        for (int i1 = 0; i1 < cn[1]; ++i1)
-            for (int i2 = 0; i2 < cn[2]; ++i2) {
-                int s = cb[0][i0] + P.nb[0] * (cb[1][i1] + P.nb[1] * cb[2][i2]);
-                T wgt = cw[0][i0] * cw[1][i1] * cw[2][i2];
+    // boxes with a non-zero weight, in a fixed order: (window offset of the node, weight)
+    constexpr int kMaxBox = 8;
+    int sb[kMaxBox];
+    int64_t lib[kMaxBox];
+    T wb[kMaxBox];
+    int nbx = 0;
+#pragma unroll
+    for (int ib = 0; ib < kMaxBox; ++ib) {
+        sb[ib] = 0;
+        lib[ib] = 0;
+        wb[ib] = T(0);
+    }
+#pragma unroll
+    for (int i0 = 0; i0 < 2; ++i0)
+#pragma unroll
+        for (int i1 = 0; i1 < 2; ++i1)
+#pragma unroll
+            for (int i2 = 0; i2 < 2; ++i2) {
+                if (i0 >= cn[0] || i1 >= cn[1] || i2 >= cn[2]) continue;
+                const int s = cb[0][i0] + P.nb[0] * (cb[1][i1] + P.nb[1] * cb[2][i2]);
+                const T wgt = cw[0][i0] * cw[1][i1] * cw[2][i2];
                 if (wgt == T(0)) continue;
                 const SubDesc& S = subs[s];
                 int64_t li = 0;
                 for (int a = ndim - 1; a >= 0; --a) li = li * S.nw[a] + (g[a] - S.lo[a]);
-                for (int l = 0; l < nsweeps; ++l) {
-                    int64_t ob = node_buf[(int64_t)l * P.nsub + s];
-                    if (ob < 0) continue;
-                    cplx<T> v = buf[ob + (int64_t)c * rstride + li];
-                    sr += (double)(wgt * v.re);
-                    si += (double)(wgt * v.im);
-                }
+#pragma unroll
+                for (int ib = 0; ib < kMaxBox; ++ib)  // register-resident list: static indices
+                    if (ib == nbx) {
+                        sb[ib] = s;
+                        lib[ib] = li;
+                        wb[ib] = wgt;
+                    }
+                ++nbx;
             }
-    U[(int64_t)c * Ng + k] = mk<double>(sr, si);
+    double sr[kAG], si[kAG];
+#pragma unroll
+    for (int c = 0; c < kAG; ++c) sr[c] = si[c] = 0;
+#pragma unroll
+    for (int ib = 0; ib < kMaxBox; ++ib) {
+        if (ib >= nbx) break;
+        for (int l = 0; l < nsweeps; ++l) {
+            const int64_t ob = node_buf[(int64_t)l * P.nsub + sb[ib]];
+            if (ob < 0) continue;
+            const cplx<T>* bp = buf + ob + lib[ib] + (int64_t)c0 * rstride;
+            cplx<T> v[kAG];
+#pragma unroll
+            for (int c = 0; c < kAG; ++c) v[c] = (c0 + c < nrhs) ? bp[(int64_t)c * rstride] : mk<T>(0, 0);
+#pragma unroll
+            for (int c = 0; c < kAG; ++c) {
+                sr[c] += (double)(wb[ib] * v[c].re);
+                si[c] += (double)(wb[ib] * v[c].im);
+            }
+        }
+    }
+#pragma unroll
+    for (int c = 0; c < kAG; ++c)
+        if (c0 + c < nrhs) U[(int64_t)(c0 + c) * Ng + k] = mk<double>(sr[c], si[c]);
 }
 
 template <typename T>
@@ -272,19 +318,19 @@ void launch_assemble(const DevProblem& P, const SubDesc* subs, const int* box_of
                      cudaStream_t st) {
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
     const int nt = 256;
-    dim3 grid((unsigned)((Ng + nt - 1) / nt), nrhs);
-    assemble_kernel<T><<<grid, nt, 0, st>>>(P, subs, box_of, node_buf, nsweeps, beta_tab, buf,
-                                             rstride, U);
+    dim3 grid((unsigned)((Ng + nt - 1) / nt), (nrhs + kAG - 1) / kAG);
+    assemble_kernel<T><<<grid, nt, 0, st>>>(P, subs, box_of, node_buf, nsweeps, beta_tab, buf, rstride, nrhs,
+                                            U);
 }
 
 template void launch_gather<float>(const Task*, int, int64_t, const SubDesc*, const Incoming*,
                                    const DevProblem&, const float*, const cplx<float>*,
                                    const cplx<float>*, const float*, const cplx<double>*, int,
-                                   cplx<float>*, int64_t, int, int, cudaStream_t);
+                                   const cplx<float>*, cplx<float>*, int64_t, int, int, cudaStream_t);
 template void launch_gather<double>(const Task*, int, int64_t, const SubDesc*, const Incoming*,
                                     const DevProblem&, const double*, const cplx<double>*,
                                     const cplx<double>*, const double*, const cplx<double>*, int,
-                                    cplx<double>*, int64_t, int, int, cudaStream_t);
+                                    const cplx<double>*, cplx<double>*, int64_t, int, int, cudaStream_t);
 template void launch_assemble<float>(const DevProblem&, const SubDesc*, const int*,
                                      const int64_t*, int, const float*, const cplx<float>*,
                                      int64_t, int, cplx<double>*, cudaStream_t);

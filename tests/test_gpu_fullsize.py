@@ -182,3 +182,26 @@ def test_adjoint_gradient_full_size(H):
             fd = (float(loss(m0 + eps * vt, 1e-12)) - float(loss(m0 - eps * vt, 1e-12))) / (2 * eps)
             dd = float(np.sum(g * v))
             assert abs(fd - dd) <= 1e-4 * abs(dd), (fd, dd)
+
+
+# ----------------------------------------------------------------------------- nonuniform
+def test_nonuniform_workload_full_size_true_residual(H):
+    """The 2088x1576 nonuniform workload (12x9 subdomains with widths 96..224;
+    windows up to 280 rows, on the mma.sync tensor-core kernel) with a sample of
+    16 of its 256 point sources: GMRES with the FP16 mode (TF32 on this kernel)
+    to a relative residual of 1e-8, checked for every right-hand side with the
+    oracle's FP64 operator."""
+    import torch
+    wl = W.config(4, src=list(range(0, 256, 16)))
+    ctx = H.helm_setup_workload(wl, precision=H.HELM_PREC_F16,
+                                stream=torch.cuda.current_stream().cuda_stream)
+    H.helm_factor(ctx)
+    U, st = H.helm_solve(ctx, torch.from_numpy(wl.f).cuda(), rtol=1e-8, maxit=60)
+    U = U.cpu().numpy()
+    ctx.close()
+    A, J = OH.global_operator(wl)
+    res = []
+    for s in range(wl.nrhs):
+        b = J * wl.f[s].ravel()
+        res.append(np.linalg.norm(b - A @ U[s].ravel()) / np.linalg.norm(b))
+    assert max(res) <= 1.5e-8, (max(res), st)

@@ -171,20 +171,22 @@ CONFIG_NAMES = {
 }
 
 
-def config(k: int, with_sources: bool = True) -> Workload:
+def config(k: int, with_sources: bool = True, src: Sequence[int] = None) -> Workload:
     """The five seismic-shaped synthetic workloads, with the sizes of the
-    paper's experiments (Section 5) scaled to one GPU."""
+    paper's experiments (Section 5) scaled to one GPU.  ``src`` keeps only the
+    sources with these indices (same positions as in the full set)."""
+    pick = (lambda xs: [xs[i] for i in src]) if src is not None else (lambda xs: list(xs))
     if k == 1:
         n, pml, h = (128, 128), 16, 1.0 / 128
         m = constant_medium(n, pml)
-        f = gaussian_sources(n, pml, h, [(0.3, 0.6)], 2 * h) if with_sources else None
+        f = gaussian_sources(n, pml, h, pick([(0.3, 0.6)]), 2 * h) if with_sources else None
         return Workload(CONFIG_NAMES[1], 2, n, h, 2 * np.pi * 8, pml, 50.0, 2, (2, 2),
                         (uniform_cuts(128, 2), uniform_cuts(128, 2)), 8, 16, m, f)
     if k == 2:
         n, pml, h = (1024, 1024), 20, 10.0
         m = layered_medium(n, pml, h, seed=2)
         nodes = [(pml + 16 * s + 8, pml + 2) for s in range(64)]
-        f = point_sources(n, pml, h, nodes) if with_sources else None
+        f = point_sources(n, pml, h, pick(nodes)) if with_sources else None
         return Workload(CONFIG_NAMES[2], 2, n, h, 2 * np.pi * 15, pml, 50.0, 2, (8, 8),
                         (uniform_cuts(1024, 8), uniform_cuts(1024, 8)), 8, 20, m, f)
     if k == 3:
@@ -192,7 +194,7 @@ def config(k: int, with_sources: bool = True) -> Workload:
         m = constant_medium(n, pml)
         rng = np.random.default_rng(3)
         centres = rng.uniform(0.125, 0.875, size=(16, 3))
-        f = gaussian_sources(n, pml, h, centres, 2 * h) if with_sources else None
+        f = gaussian_sources(n, pml, h, pick(list(centres)), 2 * h) if with_sources else None
         cuts = tuple(uniform_cuts(64, 4) for _ in range(3))
         return Workload(CONFIG_NAMES[3], 3, n, h, 2 * np.pi * 8, pml, 50.0, 2, (4, 4, 4),
                         cuts, 2, 6, m, f)
@@ -202,7 +204,7 @@ def config(k: int, with_sources: bool = True) -> Workload:
         rng = np.random.default_rng(41)
         xs = np.sort(rng.integers(0, n[0], size=256))
         nodes = [(pml + int(x), pml + 2) for x in xs]
-        f = point_sources(n, pml, h, nodes) if with_sources else None
+        f = point_sources(n, pml, h, pick(nodes)) if with_sources else None
         cuts = (random_cuts(2048, 12, 96, 224, seed=40), random_cuts(1536, 9, 96, 224, seed=40))
         return Workload(CONFIG_NAMES[4], 2, n, h, 2 * np.pi * 20, pml, 50.0, 2, (12, 9),
                         cuts, 8, 20, m, f)
@@ -213,9 +215,9 @@ def config(k: int, with_sources: bool = True) -> Workload:
         xc = (n[0] * h / 2, n[1] * h / 2)
         bump = np.exp(-((X[0] - xc[0]) ** 2 + (X[1] - xc[1]) ** 2) / (2 * 50.0 ** 2))
         m_true = m0 * (1.0 + 0.05 * bump)
-        src = [(pml + int((s + 0.5) * n[0] / 32), pml + 2) for s in range(32)]
+        shots = [(pml + int((s + 0.5) * n[0] / 32), pml + 2) for s in range(32)]
         rec = np.array([(pml + int((r + 0.5) * n[0] / 256), pml + 2) for r in range(256)])
-        f = point_sources(n, pml, h, src) if with_sources else None
+        f = point_sources(n, pml, h, pick(shots)) if with_sources else None
         return Workload(CONFIG_NAMES[5], 2, n, h, 2 * np.pi * 10, pml, 50.0, 2, (4, 4),
                         (uniform_cuts(512, 4), uniform_cuts(512, 4)), 8, 16, m0, f,
                         receivers=rec, meta={"m_true": m_true})

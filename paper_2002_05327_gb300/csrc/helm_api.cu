@@ -135,6 +135,7 @@ struct helm_ctx {
     int64_t* ufac_off = nullptr;       // byte offset per subdomain
     int umma_mt = 0;                   // CTAs per block in the tcgen05 solve (0: not used)
     int umma_nblk = 0;                 // largest block of the tcgen05 solve
+    int umma_lines = 0;                // most lines of a subdomain (twisted solve)
     bool umma_twist = false;           // tcgen05 solve in its twisted (two-ended) form
     bool f16 = false;                  // HELM_PREC_F16: FP16 operands in the twisted solve
     int* ascale_d = nullptr;           // per (subdomain, line) exponent of the FP16 factor scale
@@ -717,7 +718,10 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
             const SubDesc& S = c->subs_h[tk.sub];
             const double n = S.nblk, nl = S.nlines, passes = 2.0 * nl - 1.0;
             gbytes += (double)S.win_elems * nrhs * es;
-            sbytes += passes * n * n * es + 4.0 * nl * n * nrhs * es;
+            // block inverses once per pass (FP16 image: 4 bytes per complex entry) + b in, y out,
+            // y in, u out
+            const double fes = (c->umma_twist && c->f16) ? 4.0 : es;
+            sbytes += passes * n * n * fes + 4.0 * nl * n * nrhs * es;
             sflops += passes * n * n * nrhs * 8.0;
         }
         if (c->prec == HELM_PREC_F64) {
@@ -744,8 +748,8 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
             }
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
             if (c->prec == HELM_PREC_TF32 && c->umma_twist)
-                launch_solve_twist(t, nt, c->subs_d, c->umma_nblk, nrhs, c->ufac, c->ufac_off, c->ascale_d,
-                                   c->f16, c->Pv32, c->inva32, buf, bsrc, rs,
+                launch_solve_twist(t, nt, c->subs_d, c->umma_nblk, c->umma_lines, nrhs, c->ufac, c->ufac_off,
+                                   c->ascale_d, c->f16, c->Pv32, c->inva32, buf, bsrc, rs,
                                    DevStatus{c->err_d, c->wait_polls}, c->stream);
             else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
                 launch_solve_umma(t, nt, c->subs_d, c->umma_nblk, nrhs, panel,
@@ -1049,13 +1053,14 @@ int helm_factor(helm_ctx* c) {
         launch_factor_f32(c->subs_d, c->P.nsub, c->nbp_max, c->P, c->m32, c->an32, c->af32,
                           static_cast<float*>(c->fac), c->err_d, c->stream);
     if (c->prec == HELM_PREC_TF32) {
-        int nblk_max = 0, nl_min = 1 << 30;
+        int nblk_max = 0, nl_min = 1 << 30, nl_max = 0;
         for (const SubDesc& S : c->subs_h) {
             nblk_max = std::max(nblk_max, S.nblk);
             nl_min = std::min(nl_min, S.nlines);
+            nl_max = std::max(nl_max, S.nlines);
         }
         const bool umma = c->cfg.tc_kernel != 1 && umma_supported(nblk_max);
-        const bool twist = umma && c->cfg.tc_kernel != 2 && twist_supported(nblk_max, nl_min);
+        const bool twist = umma && c->cfg.tc_kernel != 2 && twist_supported(nblk_max, nl_min, nl_max);
         float* fac2 = nullptr;
         if (twist) {
             // the far half of every subdomain's lines, eliminated from the far end
@@ -1070,6 +1075,7 @@ int helm_factor(helm_ctx* c) {
             c->umma_twist = twist;
             c->umma_mt = twist ? 1 : umma_tiles(nblk_max);
             c->umma_nblk = nblk_max;
+            c->umma_lines = nl_max;
             const bool f16 = twist && c->f16;
             std::vector<int64_t> off;
             int64_t tot = 0;
@@ -1234,8 +1240,9 @@ int helm_subdomain_solve(helm_ctx* c, int s, int nrhs, const void* R, void* U, i
                              static_cast<cplx<double>*>(wb), static_cast<cplx<double>*>(wb), we,
                              DevStatus{c->err_d, c->wait_polls}, c->stream);
     else if (c->prec == HELM_PREC_TF32 && c->umma_twist)
-        launch_solve_twist(td, 1, c->subs_d, c->umma_nblk, nrhs, c->ufac, c->ufac_off, c->ascale_d, c->f16,
-                           c->Pv32, c->inva32, static_cast<cplx<float>*>(wb), static_cast<cplx<float>*>(wb),
+        launch_solve_twist(td, 1, c->subs_d, c->umma_nblk, c->umma_lines, nrhs, c->ufac, c->ufac_off,
+                           c->ascale_d, c->f16, c->Pv32, c->inva32, static_cast<cplx<float>*>(wb),
+                           static_cast<cplx<float>*>(wb),
                            we, DevStatus{c->err_d, c->wait_polls}, c->stream);
     else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
         launch_solve_umma(td, 1, c->subs_d, c->umma_nblk, nrhs, panel,

@@ -198,14 +198,14 @@ void launch_repack_umma(const SubDesc* subs_d, const std::vector<SubDesc>& subs_
 // nlines >= 4); factors repacked with one slice (CR = 1) from the twisted factors.
 // With f16 the image is FP16 (K chunks of 64) with per-line power-of-two
 // scales ascale[inva_off + line] (launch_line_scales, launch_repack_f16).
-bool twist_supported(int nblk_max, int nlines_min);
+bool twist_supported(int nblk_max, int nlines_min, int nlines_max);
 int64_t twist_f16_factor_bytes(const SubDesc& S);
 void launch_line_scales(const SubDesc* subs_d, int nsub, int max_lines, const float* fac, const float* fac2,
                         int* ascale, cudaStream_t st);
 void launch_repack_f16(const SubDesc* subs_d, const std::vector<SubDesc>& subs_h, const float* fac,
                        const float* fac2, const int* ascale, const int64_t* dst_off_d, void* dst,
                        cudaStream_t st);
-void launch_solve_twist(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
+void launch_solve_twist(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nlines_max, int nrhs,
                         const void* afac, const int64_t* afac_off, const int* ascale, bool f16,
                         const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf,
                         const cplx<float>* bsrc, int64_t rstride, DevStatus ds, cudaStream_t st);

@@ -888,6 +888,15 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
     const uint32_t b_bytes = (uint32_t)(nkc * kBChunkBytes);
     const uint32_t x_bytes = (uint32_t)R * PG * 8;  // middle vector: R rows x PG complex
     const int nsteps = rank == 0 ? 2 * mid + 1 : 2 * nb;
+    // Whole-line ring: when one line of factors fits (chunk li in stage li, the
+    // second tile's reads of the last chunk included), producer / issuer pair q
+    // owns the contiguous chunks [q*cpp, q*cpp + cpp) and moves them with ONE
+    // bulk copy per step (copies issued by one warp complete one after another,
+    // so fewer, larger copies arrive sooner); otherwise the chunks are dealt
+    // round-robin over kTwP sub-rings of NS/kTwP stages.
+    const bool whole = (uint32_t)(nkc - 1) * stage_bytes + 2u * (uint32_t)kTileBytes <= ring_bytes;
+    const int cpp = (nkc + kTwP - 1) / kTwP;
+    const int nq_act = whole ? (nkc + cpp - 1) / cpp : (nkc < kTwP ? nkc : kTwP);  // issuers with chunks
     // line of step s of this CTA
     auto line_of = [&](int st) -> int {
         if (rank == 0) return st < mid ? st : (st == mid ? mid : 2 * mid - st);
@@ -904,7 +913,11 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
     cplx<float>* xs = reinterpret_cast<cplx<float>*>(gbase + ring_bytes + b_bytes);
     const uint32_t xi0 = xs0 + x_bytes;
     const cplx<float>* xi = reinterpret_cast<const cplx<float>*>(gbase + ring_bytes + b_bytes + x_bytes);
-    const uint32_t bars = (xi0 + x_bytes + 7u) & ~7u;
+    // per-line scalars: 1/alpha at the nl+1 faces, then the FP16 line scales
+    const uint32_t ls0 = xi0 + x_bytes;
+    cplx<float>* ia_s = reinterpret_cast<cplx<float>*>(gbase + (ls0 - base));
+    int* as_s = reinterpret_cast<int*>(gbase + (ls0 - base) + (uint32_t)(nl + 1) * 8u);
+    const uint32_t bars = (ls0 + (uint32_t)(nl + 1) * 8u + (uint32_t)nl * 4u + 7u) & ~7u;
     uint64_t* bars_g = reinterpret_cast<uint64_t*>(gbase + (bars - base));
     auto full = [&](int s) { return bars + 8u * s; };
     auto empty = [&](int s) { return bars + 8u * (NS + s); };
@@ -916,7 +929,7 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
     volatile int* x_sent = reinterpret_cast<volatile int*>(tmem_slot + 2);  // this CTA sent its middle copy
     volatile int* x_peer = reinterpret_cast<volatile int*>(tmem_slot + 3);  // the peer sent its (exit)
-    uint32_t* s_red = tmem_slot + 4;  // [kTwEpi][PG] column maxima (F16 scales)
+    uint32_t* s_red = tmem_slot + 4;  // [2][kTwEpi][PG] column maxima (F16 scales), by step parity
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     constexpr uint32_t kCols = 2 * kTwP * kN <= 32 ? 32 : 2 * kTwP * kN <= 64 ? 64 :
@@ -931,7 +944,7 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
             mb_init(empty(s), 1);
         }
         mb_init(acc_full, kTwP);
-        mb_init(b_ready, 1);
+        mb_init(b_ready, kTwEpi);  // one arrival per epilogue warp
         mb_init(x_in, 1);
         mb_init(drain, kTwP);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -959,7 +972,26 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
     if (warp >= kTwWarpProd && warp < kTwWarpProd + kTwP) {
         // ====================================================== producers
         const int pq = warp - kTwWarpProd;
-        if (lane == 0) {
+        if (lane == 0 && whole) {
+            const char* abase = afac + afac_off[tk.sub];
+            const int c0q = pq * cpp, cnt = nkc - c0q < cpp ? nkc - c0q : cpp;
+            int issued = 0;
+            for (int step = 0; cnt > 0 && step < nsteps && !*abort_flag; ++step) {
+                const int j = line_of(step);
+                if (step > 0 && !mb_wait(empty(pq), (uint32_t)((step - 1) & 1), ds.polls)) {
+                    atomicExch(ds.err, 2);
+                    *abort_flag = 1;
+                }
+                if (*abort_flag) break;
+                mb_expect_tx(full(pq), (uint32_t)cnt * stage_bytes);
+                bulk_g2s(stage0 + (uint32_t)c0q * stage_bytes,
+                         abase + (int64_t)j * line_bytes + (int64_t)c0q * stage_bytes, (uint32_t)cnt * stage_bytes,
+                         full(pq));
+                issued = step + 1;
+            }
+            // drain: the last copy lands (every earlier one was consumed)
+            if (issued > 0) mb_wait(full(pq), (uint32_t)((issued - 1) & 1), kWait);
+        } else if (lane == 0) {
             const char* abase = afac + afac_off[tk.sub];
             int k = 0;
             for (int step = 0; step < nsteps && !*abort_flag; ++step) {
@@ -995,6 +1027,38 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
                 }
                 tc_fence_after();
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                if (whole) {
+                    const int c0q = q * cpp, cnt = nkc - c0q < cpp ? nkc - c0q : cpp;
+                    if (cnt > 0) {
+                        if (!mb_wait(full(q), (uint32_t)(step & 1), ds.polls)) {
+                            atomicExch(ds.err, 2);
+                            *abort_flag = 1;
+                            break;
+                        }
+                        tc_fence_after();
+                        for (int i = 0; i < cnt; ++i) {
+                            const int li = c0q + i;
+                            const uint64_t bdesc = bdesc0 + (uint64_t)(li * (kBChunkBytes >> 4));
+                            for (int t = 0; t < ntile; ++t) {
+                                const uint64_t adesc =
+                                    desc_sw128(stage0 + (uint32_t)li * stage_bytes + (uint32_t)t * kTileBytes);
+                                const uint32_t dacc = tmem + (uint32_t)((t * kTwP + q) * kN);
+#pragma unroll
+                                for (int kk = 0; kk < 4; ++kk) {
+                                    if constexpr (F16)
+                                        umma_f16(dacc, adesc + (uint64_t)(2 * kk), bdesc + (uint64_t)(2 * kk),
+                                                 idesc, (i == 0 && kk == 0) ? 0u : 1u);
+                                    else
+                                        umma_tf32(dacc, adesc + (uint64_t)(2 * kk), bdesc + (uint64_t)(2 * kk),
+                                                  idesc, (i == 0 && kk == 0) ? 0u : 1u);
+                                }
+                            }
+                        }
+                        umma_commit(empty(q));
+                    }
+                    umma_commit(acc_full);
+                    continue;
+                }
                 bool first = true;
                 for (int li = q; li < nkc; li += kTwP) {
                     const int s = q * NQ + k % NQ;
@@ -1037,7 +1101,6 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
         const int n4 = (n + 3) & ~3;
         const bool wr = p < n4 && t < ntile;  // writes B rows 2p, 2p+1
         const cplx<float> pvp = rv ? Pv[S.coup_off + p] : mk<float>(0, 0);
-        const cplx<float>* ia = inva + S.inva_off;
         cplx<float>* V = buf + tk.buf_off;
         const int c0 = blockIdx.y * PG;
         int ncol = nrhs - c0;
@@ -1051,7 +1114,7 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
             else
                 return (uint32_t)(kcb * kBChunkBytes + row * 128 + (((kkb / 4) ^ (row % 8)) * 16) + (kkb % 4) * 4);
         };
-        auto coup = [&](int face) -> cplx<float> { return rv ? pvp * ia[face] : mk<float>(0, 0); };
+        auto coup = [&](int face) -> cplx<float> { return rv ? pvp * ia_s[face] : mk<float>(0, 0); };
         int sbv[PG];  // F16: exponent of the scale of each column of the current B
 #pragma unroll
         for (int c = 0; c < PG; ++c) sbv[c] = 0;
@@ -1069,24 +1132,28 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
             for (int c = 0; c < PG; ++c)
                 if (rv && c < ncol) V[(int64_t)(c0 + c) * rstride + (int64_t)j * n + p] = v[c];
         };
-        // B of the next step: rows 2c (Re r, -Im r) and 2c+1 (Im r, Re r), TF32; then
-        // (writers' stores before the tensor cores' reads, TMEM loads before the
-        // thread sync) one arrival on b_ready
-        auto announce = [&](const cplx<float> (&v)[PG]) {
+        // B of the next step: rows 2c (Re r, -Im r) and 2c+1 (Im r, Re r); the
+        // epilogue's one barrier of the step (which also takes the uniform abort
+        // decision over the step's waits, and for FP16 combines the column
+        // maxima into the scale exponents) comes before any B write; then each
+        // warp, its stores made visible to the tensor cores and its TMEM loads
+        // ordered, arrives on b_ready.  False: some thread's wait failed.
+        int ann = 0;
+        auto announce = [&](const cplx<float> (&v)[PG], bool bad) -> bool {
             if constexpr (F16) {
-                // column maxima over the CTA's rows -> scale exponents
+                uint32_t* sr = s_red + (ann & 1) * (kTwEpi * PG);
 #pragma unroll
                 for (int c = 0; c < PG; ++c) {
                     const float m = rv ? fmaxf(fabsf(v[c].re), fabsf(v[c].im)) : 0.f;
                     const uint32_t wmx = __reduce_max_sync(0xffffffffu, __float_as_uint(m));
-                    if (lane == 0) s_red[warp * PG + c] = wmx;
+                    if (lane == 0) sr[warp * PG + c] = wmx;
                 }
-                epi_sync(kTwEpiThreads);
+                if (epi_any(bad, kTwEpiThreads)) return false;
 #pragma unroll
                 for (int c = 0; c < PG; ++c) {
                     uint32_t mx = 0;
 #pragma unroll
-                    for (int w = 0; w < kTwEpi; ++w) mx = max(mx, s_red[w * PG + c]);
+                    for (int w = 0; w < kTwEpi; ++w) mx = max(mx, sr[w * PG + c]);
                     int sc = 0;
                     if (mx != 0 && mx < 0x7F800000u) {
                         sc = 13 - ((int)((mx >> 23) & 0xFF) - 127);
@@ -1104,19 +1171,24 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
                         *reinterpret_cast<__half2*>(bh + boff(2 * c + 1) / 2) = __floats2half2_rn(im, re);
                     }
                 }
-            } else if (wr) {
+            } else {
+                if (epi_any(bad, kTwEpiThreads)) return false;
+                if (wr) {
 #pragma unroll
-                for (int c = 0; c < PG; ++c) {
-                    const float re = __uint_as_float(to_tf32(v[c].re)), im = __uint_as_float(to_tf32(v[c].im));
-                    const float nim = __uint_as_float(to_tf32(-v[c].im));
-                    *reinterpret_cast<float2*>(bl + boff(2 * c) / 4) = make_float2(re, nim);
-                    *reinterpret_cast<float2*>(bl + boff(2 * c + 1) / 4) = make_float2(im, re);
+                    for (int c = 0; c < PG; ++c) {
+                        const float re = __uint_as_float(to_tf32(v[c].re)), im = __uint_as_float(to_tf32(v[c].im));
+                        const float nim = __uint_as_float(to_tf32(-v[c].im));
+                        *reinterpret_cast<float2*>(bl + boff(2 * c) / 4) = make_float2(re, nim);
+                        *reinterpret_cast<float2*>(bl + boff(2 * c + 1) / 4) = make_float2(im, re);
+                    }
                 }
             }
+            ++ann;
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             tc_fence_before();
-            epi_sync(kTwEpiThreads);
-            if (tid == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b_ready) : "memory");
+            __syncwarp();
+            if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b_ready) : "memory");
+            return true;
         };
         // middle vector to the peer: rows of this CTA into x_stage, one bulk copy
         auto send_middle = [&](const cplx<float> (&v)[PG]) {
@@ -1150,19 +1222,21 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
         // the forward steps' operand is the source b, the backward steps' their y / z
         auto pre_is_b = [&](int st) -> bool { return rank == 0 ? st < mid : st < nb; };
         cplx<float> pre[PG], pre_next[PG], outv[PG], nbv[PG], xv[PG];
-        bool ok = true;
+        // this subdomain's per-line scalars into shared memory (off the step chain)
+        for (int f = tid; f <= nl; f += kTwEpiThreads) ia_s[f] = inva[S.inva_off + f];
+        if constexpr (F16)
+            for (int f = tid; f < nl; f += kTwEpiThreads) as_s[f] = ascale[S.inva_off + f];
         // first B: b_0 (top) or b_{nl-1} (bottom)
         vload(rank == 0 ? 0 : nl - 1, true, nbv);
         vload(pre_line(0), pre_is_b(0), pre);
-        announce(nbv);
-        for (int step = 0; step < nsteps; ++step) {
+        epi_sync(kTwEpiThreads);
+        bool ok = announce(nbv, false);
+        for (int step = 0; ok && step < nsteps; ++step) {
             const int j = line_of(step);
             vload(pre_line(step + 1), pre_is_b(step + 1), pre_next);
-            bool bad = *abort_flag || !mb_wait(acc_full, (uint32_t)(step & 1), ds.polls);
-            if (epi_any(bad, kTwEpiThreads)) {
-                ok = false;
-                break;
-            }
+            // a failed wait is acted on at the step's barrier (uniformly); the
+            // TMEM loads below stay within this CTA's allocation either way
+            const bool bad = *abort_flag || !mb_wait(acc_full, (uint32_t)(step & 1), ds.polls);
             tc_fence_after();
             float acc[kN];
 #pragma unroll
@@ -1173,7 +1247,7 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
                 for (int q = 0; q < kTwP; ++q)
 #pragma unroll
                     for (int h = 0; h < kN / 16; ++h)
-                        if (q < nkc)
+                        if (q < nq_act)
                             tmem_ld16_async(tmem + ((uint32_t)(quarter * 32) << 16) +
                                                 (uint32_t)(((t < ntile ? t : 0) * kTwP + q) * kN + 16 * h),
                                             part[q][h]);
@@ -1182,7 +1256,7 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
                 for (int q = 0; q < kTwP; ++q)
 #pragma unroll
                     for (int h = 0; h < kN / 16; ++h) {
-                        if (q >= nkc) continue;
+                        if (q >= nq_act) continue;
                         tmem_pin16(part[q][h]);
 #pragma unroll
                         for (int e = 0; e < 16; ++e) acc[16 * h + e] += __uint_as_float(part[q][h][e]);
@@ -1190,7 +1264,7 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
             }
             cplx<float> y[PG];
             if constexpr (F16) {
-                const int sa = ascale[S.inva_off + j];
+                const int sa = as_s[j];
 #pragma unroll
                 for (int c = 0; c < PG; ++c) {
                     const float us = pow2f(-(sa + sbv[c]));
@@ -1262,7 +1336,10 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
                     }
                 }
             }
-            if (!last) announce(nbv);
+            if (last ? epi_any(bad, kTwEpiThreads) : !announce(nbv, bad)) {
+                ok = false;
+                break;
+            }
             vstore(j, outv);
 #pragma unroll
             for (int c = 0; c < PG; ++c) pre[c] = pre_next[c];
@@ -1293,9 +1370,9 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
 
 // Shared-memory plan of a twisted launch: ns stages (kTwP sub-rings of at
 // least 2) of R*128 bytes plus the 256-row tail of the last one, B, the two
-// middle buffers, barriers, slots and the column-maximum scratch, alignment;
-// 0 if it does not fit.
-static size_t twist_smem_plan(int PG, bool f16, int nblk_max, int* ns_out, uint32_t* ring_out) {
+// middle buffers, the per-line scalars, barriers, slots and the column-maximum
+// scratch, alignment; 0 if it does not fit.
+static size_t twist_smem_plan(int PG, bool f16, int nblk_max, int nlines_max, int* ns_out, uint32_t* ring_out) {
     const int kTwP = tw_pairs(f16);
     int nkc = 0;
     if (f16)
@@ -1304,22 +1381,24 @@ static size_t twist_smem_plan(int PG, bool f16, int nblk_max, int* ns_out, uint3
         umma_line_bytes(nblk_max, 1, &nkc);
     const size_t sb = (size_t)umma_rows(nblk_max, 1) * 128;
     const size_t tail = 2 * (size_t)kTileBytes;  // the second tile's MMA reads 128 rows from +16 KB
-    const size_t fixed = (size_t)nkc * 2 * PG * 128 + 2 * (size_t)umma_rows(nblk_max, 1) * PG * 8 + 1024 + 1024;
+    const size_t lines = (size_t)(nlines_max + 1) * 8 + (size_t)nlines_max * 4;
+    const size_t fixed =
+        (size_t)nkc * 2 * PG * 128 + 2 * (size_t)umma_rows(nblk_max, 1) * PG * 8 + lines + 1024 + 1024;
     const size_t budget = 227 * 1024;
     if (fixed + (2 * kTwP - 1) * sb + tail > budget) return 0;
     int ns = (int)((budget - fixed - tail) / sb) + 1;
-    if (ns > 30) ns = 30;  // barriers, slots and the scratch within the 1 KB reserve
+    if (ns > 28) ns = 28;  // (2 ns + 4) barriers, 4 slots and the 2 x 8 x PG scratch within the 1 KB reserve
     ns -= ns % kTwP;
     *ns_out = ns;
     *ring_out = (uint32_t)((ns - 1) * sb + tail);
     return *ring_out + fixed;
 }
 
-bool twist_supported(int nblk_max, int nlines_min) {
+bool twist_supported(int nblk_max, int nlines_min, int nlines_max) {
     int ns;
     uint32_t ring;
-    return nblk_max <= 256 && nlines_min >= 4 && twist_smem_plan(8, false, nblk_max, &ns, &ring) != 0 &&
-           twist_smem_plan(8, true, nblk_max, &ns, &ring) != 0;
+    return nblk_max <= 256 && nlines_min >= 4 && twist_smem_plan(8, false, nblk_max, nlines_max, &ns, &ring) != 0 &&
+           twist_smem_plan(8, true, nblk_max, nlines_max, &ns, &ring) != 0;
 }
 
 int64_t twist_f16_factor_bytes(const SubDesc& S) { return umma_line_bytes16(S.nblk, nullptr) * S.nlines; }
@@ -1340,14 +1419,14 @@ void launch_repack_f16(const SubDesc* subs_d, const std::vector<SubDesc>& subs_h
 }
 
 template <bool F16>
-static void launch_twist_t(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
+static void launch_twist_t(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nlines_max, int nrhs,
                            const void* afac, const int64_t* afac_off, const int* ascale, const cplx<float>* Pv,
                            const cplx<float>* inva, cplx<float>* buf, const cplx<float>* bsrc, int64_t rstride,
                            DevStatus ds, cudaStream_t st) {
     constexpr int PG = 8;
     int ns = 0;
     uint32_t ring = 0;
-    const size_t smem = twist_smem_plan(PG, F16, nblk_max, &ns, &ring);
+    const size_t smem = twist_smem_plan(PG, F16, nblk_max, nlines_max, &ns, &ring);
     cudaFuncSetAttribute(solve_twist_kernel<PG, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ntask * 2, (nrhs + PG - 1) / PG, 1);
@@ -1365,16 +1444,16 @@ static void launch_twist_t(const Task* tasks, int ntask, const SubDesc* subs, in
                        buf, bsrc, rstride, ns, ring, ds);
 }
 
-void launch_solve_twist(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nrhs,
+void launch_solve_twist(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nlines_max, int nrhs,
                         const void* afac, const int64_t* afac_off, const int* ascale, bool f16,
                         const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf,
                         const cplx<float>* bsrc, int64_t rstride, DevStatus ds, cudaStream_t st) {
     if (ntask == 0) return;
     if (f16)
-        launch_twist_t<true>(tasks, ntask, subs, nblk_max, nrhs, afac, afac_off, ascale, Pv, inva, buf, bsrc,
+        launch_twist_t<true>(tasks, ntask, subs, nblk_max, nlines_max, nrhs, afac, afac_off, ascale, Pv, inva, buf, bsrc,
                              rstride, ds, st);
     else
-        launch_twist_t<false>(tasks, ntask, subs, nblk_max, nrhs, afac, afac_off, ascale, Pv, inva, buf, bsrc,
+        launch_twist_t<false>(tasks, ntask, subs, nblk_max, nlines_max, nrhs, afac, afac_off, ascale, Pv, inva, buf, bsrc,
                               rstride, ds, st);
 }
 

@@ -10,83 +10,18 @@
 // combinations, norms) keep their vectors in FP64 but do their arithmetic in
 // float-float ("double-float" pairs hi + lo) on the FP32 pipes: on this GPU
 // the FP64 pipe issues about one sixty-fourth of the FP32 rate, and the FP64
-// versions of these kernels ran at ~87% of it.  A double is split exactly into its top 24 and next 24
-// mantissa bits with integer operations only (conversions from double would
-// use the FP64 pipe); products are formed exactly with FMA (TwoProd) and sums
-// are compensated (TwoSum), so a dot or combination carries ~48 significant
-// bits -- ample for an Arnoldi relation to the 1e-8 residual the solver
-// targets.  Results go back to FP64 as hi + lo.
+// versions of these kernels ran at ~87% of it.  A double is split exactly
+// into its top 24 and next 24 mantissa bits, and a result recombined, with
+// integer operations only (ff.h: conversions and additions in FP64 would use
+// the FP64 pipe); products are formed exactly with FMA (TwoProd) and sums are
+// compensated (TwoSum), so a dot or combination carries ~48 significant bits
+// -- ample for an Arnoldi relation to the 1e-8 residual the solver targets.
 #include "helm_internal.h"
+#include "ff.h"
 
 namespace helm {
 
-namespace {
-
-struct ff {
-    float hi, lo;
-};
-
-// x = hi + lo exactly up to the 5 lowest mantissa bits of x (48 of 53 bits
-// kept); values below 2^-126 (and the low part below 2^-75) read as 0, which
-// is far under anything these vectors hold.  Integer and FP32 operations only.
-__device__ __forceinline__ ff split_d(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned int sign = (unsigned int)(b >> 32) & 0x80000000u;
-    const int e = (int)((b >> 52) & 0x7FF);
-    const int ef = e - 1023 + 127;
-    if (e == 0x7FF) return {x != x ? __int_as_float(0x7FC00000) : __int_as_float((int)(sign | 0x7F800000u)), 0.f};
-    if (ef <= 0) return {0.f, 0.f};
-    if (ef >= 255) return {__int_as_float((int)(sign | 0x7F800000u)), 0.f};
-    const unsigned long long m = b & 0xFFFFFFFFFFFFFull;
-    const float hi = __uint_as_float(sign | ((unsigned int)ef << 23) | (unsigned int)(m >> 29));
-    const int es = e - 948;  // float exponent field of 2^(e - 1075), the weight of the low 29 bits
-    float lo = 0.f;
-    if (es > 0) lo = __uint2float_rn((unsigned int)(m & 0x1FFFFFFFull)) * __uint_as_float((unsigned int)es << 23);
-    return {hi, sign ? -lo : lo};
-}
-// exact float -> double through the bits (normal floats; zero and values below
-// 2^-126 give 0): keeps the conversion off the FP64 pipe
-__device__ __forceinline__ double f2d(float f) {
-    const unsigned int u = __float_as_uint(f);
-    const unsigned int e = (u >> 23) & 0xFF;
-    if (e == 0) return 0.0;
-    if (e == 0xFF) return (double)f;
-    const unsigned long long b = ((unsigned long long)(u >> 31) << 63) |
-                                 ((unsigned long long)(e - 127 + 1023) << 52) |
-                                 ((unsigned long long)(u & 0x7FFFFFu) << 29);
-    return __longlong_as_double((long long)b);
-}
-__device__ __forceinline__ double join_d(ff a) { return f2d(a.hi) + f2d(a.lo); }
-
-// s += p with p's rounding error carried into the low word (Knuth's TwoSum)
-__device__ __forceinline__ void acc_add(ff& s, float p) {
-    const float t = s.hi + p;
-    const float v = t - s.hi;
-    const float e = (s.hi - (t - v)) + (p - v);
-    s.hi = t;
-    s.lo += e;
-}
-// s += a * b for a, b float-float: the head product exactly (TwoProd), the
-// cross terms and the tail into the low word
-__device__ __forceinline__ void acc_mul(ff& s, ff a, ff b) {
-    const float p = a.hi * b.hi;
-    const float e = fmaf(a.hi, b.hi, -p);
-    acc_add(s, p);
-    s.lo += fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
-}
-__device__ __forceinline__ ff ff_neg(ff a) { return {-a.hi, -a.lo}; }
-// a + b of two accumulators (tree reductions)
-__device__ __forceinline__ ff ff_sum(ff a, ff b) {
-    ff s = a;
-    acc_add(s, b.hi);
-    s.lo += b.lo;
-    return s;
-}
-__device__ __forceinline__ ff shfl_down_ff(ff a, int o) {
-    return {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
-}
-
-}  // namespace
+using namespace ffa;
 
 __device__ __forceinline__ void unflat(int64_t k, const int N[3], int g[3]) {
     g[0] = (int)(k % N[0]);

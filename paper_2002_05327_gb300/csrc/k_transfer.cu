@@ -15,6 +15,7 @@
 // assemble: u_DDM = sum_l sum_ij beta_{0,0;ij} u^l_ij (Eq. 3.x / 4.x), summed
 // per global node over the at most 2^n boxes whose cutoff reaches it.
 #include "helm_internal.h"
+#include "ff.h"
 
 namespace helm {
 
@@ -286,9 +287,16 @@ __global__ void assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs,
                     }
                 ++nbx;
             }
+    // complex64 windows: float-float sums (no FP64 instruction per term);
+    // complex128 windows: doubles
+    constexpr bool kF32 = sizeof(T) == 4;
     double sr[kAG], si[kAG];
+    ffa::ff fr[kAG], fi[kAG];
 #pragma unroll
-    for (int c = 0; c < kAG; ++c) sr[c] = si[c] = 0;
+    for (int c = 0; c < kAG; ++c) {
+        sr[c] = si[c] = 0;
+        fr[c] = fi[c] = ffa::ff{0.f, 0.f};
+    }
 #pragma unroll
     for (int ib = 0; ib < kMaxBox; ++ib) {
         if (ib >= nbx) break;
@@ -301,14 +309,24 @@ __global__ void assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs,
             for (int c = 0; c < kAG; ++c) v[c] = (c0 + c < nrhs) ? bp[(int64_t)c * rstride] : mk<T>(0, 0);
 #pragma unroll
             for (int c = 0; c < kAG; ++c) {
-                sr[c] += (double)(wb[ib] * v[c].re);
-                si[c] += (double)(wb[ib] * v[c].im);
+                if constexpr (kF32) {
+                    ffa::acc_add(fr[c], wb[ib] * v[c].re);
+                    ffa::acc_add(fi[c], wb[ib] * v[c].im);
+                } else {
+                    sr[c] += wb[ib] * v[c].re;
+                    si[c] += wb[ib] * v[c].im;
+                }
             }
         }
     }
 #pragma unroll
-    for (int c = 0; c < kAG; ++c)
-        if (c0 + c < nrhs) U[(int64_t)(c0 + c) * Ng + k] = mk<double>(sr[c], si[c]);
+    for (int c = 0; c < kAG; ++c) {
+        if (c0 + c >= nrhs) continue;
+        if constexpr (kF32)
+            U[(int64_t)(c0 + c) * Ng + k] = mk<double>(ffa::join_d(fr[c]), ffa::join_d(fi[c]));
+        else
+            U[(int64_t)(c0 + c) * Ng + k] = mk<double>(sr[c], si[c]);
+    }
 }
 
 template <typename T>

@@ -34,6 +34,13 @@ __device__ __forceinline__ ff split_d(double x) {
     return {hi, sign ? -lo : lo};
 }
 
+// double -> float rounded to nearest (up to one unit where the low part's own
+// rounding meets a tie), without the FP64 pipe
+__device__ __forceinline__ float d2f(double x) {
+    const ff s = split_d(x);
+    return s.hi + s.lo;
+}
+
 // exact float -> double through the bits (zero and values below 2^-126 give
 // a signed zero)
 __device__ __forceinline__ double f2d(float f) {

@@ -106,13 +106,11 @@ struct helm_ctx {
     std::vector<SubDesc> subs_h;
     SubDesc* subs_d = nullptr;
     int nbp_max = 0;
-    int64_t max_win = 0;
-    int max_nw0 = 0;       // largest window extent along x
-    int max_lines12 = 0;   // largest number of x-lines (nw[1]*nw[2]) of a window
 
     // global problem
     cplx<double>* g_alpha = nullptr;  // per axis: nodes then faces
     Win<double> gwin{};
+    float4* stc_d = nullptr;           // per node: the J-multiplied stencil, float-float
     double* m64 = nullptr;
     float* m32 = nullptr;
     int64_t Ng = 0;
@@ -154,6 +152,10 @@ struct helm_ctx {
     std::vector<int> level_off;
     Task* tasks_d = nullptr;
     Incoming* inc_d = nullptr;
+    GNode* gnode_d = nullptr;          // gather work list (nodes)
+    GBlock* gblk_d = nullptr;          // gather work list (blocks, level after level)
+    std::vector<int> gblk_off;         // first block of each level, and the total
+    std::vector<int64_t> gnodes_lv;    // work-list nodes per level
     std::vector<int64_t> node_buf_h;  // (l*nsub + s) -> element offset, or -1 if inactive
     int64_t* node_buf_d = nullptr;
     int64_t buf_per_rhs = 0;
@@ -349,6 +351,72 @@ int upload(T** dst, const void* src, size_t bytes, helm_ctx* c) {
     return HELM_OK;
 }
 
+// Gather work list (k_transfer.cu): per task, in level order, the window
+// nodes the first sweep's box or an incoming transfer's strip reaches.  A
+// strip is a box of nodes: along each axis the transfer points through, the
+// d + 1 nodes beyond the sender's box face (the receiver evaluates
+// -A_recv(beta v) there; beta vanishes from the d-th node on and its residual
+// reaches one node further); along the other axes, the whole window.
+int build_gather_list(helm_ctx* c, const std::vector<Task>& tasks, const std::vector<Incoming>& inc) {
+    const int ndim = c->P.ndim, d = c->P.d;
+    std::vector<GNode> nodes;
+    std::vector<GBlock> blocks;
+    std::vector<uint32_t> mark;
+    c->gblk_off.clear();
+    c->gnodes_lv.clear();
+    for (size_t lv = 0; lv + 1 < c->level_off.size(); ++lv) {
+        c->gblk_off.push_back((int)blocks.size());
+        const int64_t lv_first = (int64_t)nodes.size();
+        for (int ti = c->level_off[lv]; ti < c->level_off[lv + 1]; ++ti) {
+            const Task& t = tasks[ti];
+            const SubDesc& S = c->subs_h[t.sub];
+            mark.assign((size_t)S.win_elems, 0u);
+            // global node ranges [lo, hi), clipped to the receiver's window
+            auto paint = [&](const int lo[3], const int hi[3], uint32_t bit) {
+                int a0[3], a1[3];
+                for (int a = 0; a < 3; ++a) {
+                    a0[a] = std::max(lo[a], S.lo[a]) - S.lo[a];
+                    a1[a] = std::min(hi[a], S.hi[a]) - S.lo[a];
+                    if (a0[a] >= a1[a]) return;
+                }
+                for (int z = a0[2]; z < a1[2]; ++z)
+                    for (int y = a0[1]; y < a1[1]; ++y)
+                        for (int x = a0[0]; x < a1[0]; ++x)
+                            mark[((size_t)z * S.nw[1] + y) * S.nw[0] + x] |= bit;
+            };
+            if (t.sweep == 0) paint(S.box_lo, S.box_hi, 1u << 31);
+            for (int i = 0; i < t.in_cnt; ++i) {
+                const Incoming& I = inc[(size_t)t.in_off + i];
+                const SubDesc& R = c->subs_h[I.sender];
+                int lo[3], hi[3];
+                for (int a = 0; a < 3; ++a) {
+                    lo[a] = S.lo[a];
+                    hi[a] = S.hi[a];
+                    if (a >= ndim) continue;
+                    if (I.dir[a] > 0) {
+                        lo[a] = R.box_hi[a];
+                        hi[a] = R.box_hi[a] + d + 1;
+                    } else if (I.dir[a] < 0) {
+                        lo[a] = R.box_lo[a] - 1 - d;
+                        hi[a] = R.box_lo[a];
+                    }
+                }
+                paint(lo, hi, 1u << i);
+            }
+            const int64_t first = (int64_t)nodes.size();
+            for (size_t k = 0; k < mark.size(); ++k)
+                if (mark[k]) nodes.push_back({(uint32_t)k, mark[k]});
+            for (int64_t n0 = first; n0 < (int64_t)nodes.size(); n0 += kGB)
+                blocks.push_back({ti, (int)std::min<int64_t>(kGB, (int64_t)nodes.size() - n0), n0});
+        }
+        c->gnodes_lv.push_back((int64_t)nodes.size() - lv_first);
+    }
+    c->gblk_off.push_back((int)blocks.size());
+    TRY(upload(&c->gnode_d, nodes.data(), nodes.size() * sizeof(GNode), c));
+    TRY(upload(&c->gblk_d, blocks.data(), blocks.size() * sizeof(GBlock), c));
+    return HELM_OK;
+}
+
 std::vector<cplx<double>> to_c128(const std::vector<cd>& v) {
     std::vector<cplx<double>> o(v.size());
     for (size_t i = 0; i < v.size(); ++i) o[i] = {v[i].real(), v[i].imag()};
@@ -440,6 +508,14 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
         std::vector<float> m32(c->Ng);
         for (int64_t i = 0; i < c->Ng; ++i) m32[i] = (float)m[i];
         TRY(upload(&c->m32, m32.data(), c->Ng * sizeof(float), c));
+    }
+    // ---- the global operator's stencil, once (operator products, residuals)
+    {
+        const size_t bytes = (size_t)c->Ng * (1 + 2 * ndim) * sizeof(float4);
+        CK(cudaMalloc(&c->stc_d, bytes));
+        c->dev_bytes += bytes;
+        launch_stencil_ff(P, c->gwin, c->m64, c->stc_d, c->stream);
+        CK(cudaGetLastError());
     }
     // ---- boxes per axis (global node ranges); edge boxes run over the global PML
     std::vector<std::vector<int>> blo(3), bhi(3);
@@ -553,9 +629,6 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
         S.inva_off = ia.size();
         for (int j = 0; j <= S.nlines; ++j) ia.push_back(1.0 / af[S.face_off[slow] + j]);
         c->nbp_max = std::max(c->nbp_max, S.nbp);
-        c->max_win = std::max(c->max_win, S.win_elems);
-        c->max_nw0 = std::max(c->max_nw0, S.nw[0]);
-        c->max_lines12 = std::max(c->max_lines12, S.nw[1] * S.nw[2]);
     }
     {
         auto a128 = to_c128(an), f128 = to_c128(af), p128 = to_c128(pv), i128 = to_c128(ia);
@@ -681,6 +754,7 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
     c->level_off.push_back((int)all_tasks.size());
     TRY(upload(&c->tasks_d, all_tasks.data(), all_tasks.size() * sizeof(Task), c));
     TRY(upload(&c->inc_d, inc_all.data(), inc_all.size() * sizeof(Incoming), c));
+    TRY(build_gather_list(c, all_tasks, inc_all));
     TRY(upload(&c->node_buf_d, c->node_buf_h.data(), c->node_buf_h.size() * 8, c));
     CK(cudaMalloc(&c->err_d, sizeof(int)));
     return HELM_OK;
@@ -713,11 +787,12 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
     for (size_t lv = 0; lv < c->levels.size(); ++lv) {
         const Task* t = c->tasks_d + c->level_off[lv];
         int nt = (int)c->levels[lv].size();
-        double gbytes = 0, sbytes = 0, sflops = 0;
+        // gather: the work list's sources written (the reads depend on the strips)
+        const double gbytes = (double)c->gnodes_lv[lv] * nrhs * es;
+        double sbytes = 0, sflops = 0;
         for (const Task& tk : c->levels[lv]) {
             const SubDesc& S = c->subs_h[tk.sub];
             const double n = S.nblk, nl = S.nlines, passes = 2.0 * nl - 1.0;
-            gbytes += (double)S.win_elems * nrhs * es;
             // block inverses once per pass (FP16 image: 4 bytes per complex entry) + b in, y out,
             // y in, u out
             const double fes = (c->umma_twist && c->f16) ? 4.0 : es;
@@ -729,9 +804,9 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
             auto* bsrc = static_cast<cplx<double>*>(c->bsrc);
             {
                 ProfScope ps(c, HELM_K_GATHER, 1, gbytes);
-                launch_gather<double>(t, nt, c->max_win, c->subs_d, c->inc_d, c->P, c->m64,
-                                      c->an64, c->af64, c->tab64, b, nrhs, buf, bsrc, rs, c->max_nw0,
-                                      c->max_lines12, c->stream);
+                launch_gather<double>(c->gblk_d + c->gblk_off[lv], c->gblk_off[lv + 1] - c->gblk_off[lv],
+                                      c->gnode_d, c->tasks_d, c->subs_d, c->inc_d, c->P, c->m64, c->an64,
+                                      c->af64, c->tab64, b, nrhs, buf, bsrc, rs, c->stream);
             }
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
             launch_solve<double>(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
@@ -742,9 +817,9 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U)
             auto* bsrc = static_cast<cplx<float>*>(c->bsrc);
             {
                 ProfScope ps(c, HELM_K_GATHER, 1, gbytes);
-                launch_gather<float>(t, nt, c->max_win, c->subs_d, c->inc_d, c->P, c->m32,
-                                     c->an32, c->af32, c->tab32, b, nrhs, buf, bsrc, rs, c->max_nw0,
-                                     c->max_lines12, c->stream);
+                launch_gather<float>(c->gblk_d + c->gblk_off[lv], c->gblk_off[lv + 1] - c->gblk_off[lv],
+                                     c->gnode_d, c->tasks_d, c->subs_d, c->inc_d, c->P, c->m32, c->an32,
+                                     c->af32, c->tab32, b, nrhs, buf, bsrc, rs, c->stream);
             }
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
             if (c->prec == HELM_PREC_TF32 && c->umma_twist)
@@ -867,7 +942,7 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
     double maxres = 0;
     bool conv = false;
     while (true) {
-        { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_apply_A(c->P, c->gwin, c->m64, b, x, w, nrhs, c->stream); }
+        { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_apply_A(c->P, c->stc_d, b, x, w, nrhs, c->stream); }
         std::vector<double> beta(nrhs);
         TRY(norms(w, beta));
         maxres = 0;
@@ -903,7 +978,10 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
             ++apps;
             // w = -A z_k (apply_A with no b); CGS2 on w: h = V^H w, w -= V h, twice.
             // Then A z_k = sum_i (-h_i) v_i + |w| v_{k+1} with v_{k+1} = -w/|w|.
-            { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_apply_A(c->P, c->gwin, c->m64, nullptr, Z(k), w, nrhs, c->stream); }
+            {
+                ProfScope ps_(c, HELM_K_KRYLOV, 1);
+                launch_apply_A(c->P, c->stc_d, nullptr, Z(k), w, nrhs, c->stream);
+            }
             std::vector<std::vector<cd>> hsum(nrhs, std::vector<cd>(k + 2, 0.0));
             {
                 std::vector<cplx<double>*> vp(k + 1);
@@ -1203,7 +1281,7 @@ int helm_residual(helm_ctx* c, int nrhs, const void* F, const void* U, void* R, 
     TRY(stage_in(c, mem == HELM_MEM_DEVICE ? R : nullptr, bytes, mem, r));
     TRY(ensure_bvec(c, nrhs));
     { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_scale_J(c->P, c->gwin, f.ptr, c->bvec, nrhs, false, c->stream); }
-    { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_apply_A(c->P, c->gwin, c->m64, c->bvec, u.ptr, r.ptr, nrhs, c->stream); }
+    { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_apply_A(c->P, c->stc_d, c->bvec, u.ptr, r.ptr, nrhs, c->stream); }
     CK(cudaGetLastError());
     return stage_out(c, R, r, bytes, mem);
 }
@@ -1349,8 +1427,10 @@ void helm_destroy(helm_ctx* c) {
     if (!c) return;
     void* ptrs[] = {c->ufac, c->ufac_off, c->subs_d, c->g_alpha, c->m64, c->m32, c->an64, c->af64, c->an32, c->af32,
                     c->Pv64, c->inva64, c->Pv32, c->inva32, c->tab64, c->tab32, c->box_of,
-                    c->fac, c->err_d, c->tasks_d, c->inc_d, c->node_buf_d, c->buf, c->bvec,
-                    c->small_d, c->partial_d, c->scal_d, c->vptr_d, c->zptr_d, c->ascale_d, c->bsrc};
+                    c->fac, c->err_d, c->tasks_d, c->inc_d, c->gnode_d, c->gblk_d, c->node_buf_d, c->buf,
+                    c->bvec,
+                    c->small_d, c->partial_d, c->scal_d, c->vptr_d, c->zptr_d, c->ascale_d, c->bsrc,
+                    c->stc_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto* p : c->gm) cudaFree(p);

@@ -214,12 +214,28 @@ void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nb
                        const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf,
                        const cplx<float>* bsrc, int64_t rstride, DevStatus ds, cudaStream_t st);
 
+// Work list of the gather: per task (in level order) the window nodes that
+// are ever written -- the first sweep's box, and every node some incoming
+// transfer's strip reaches -- in window order, each with the transfers that
+// reach it (bit i: the task's i-th incoming transfer; bit 31: in the first
+// sweep's box).  Blocks take up to kGB consecutive nodes of one task.
+// launch_gather reads the senders' solutions in buf and writes the local
+// sources into bsrc.
+constexpr int kGB = 128;
+struct GNode {
+    uint32_t k;     // window-linear node index
+    uint32_t mask;
+};
+struct GBlock {
+    int task;       // index into the level-ordered task array
+    int cnt;        // nodes (<= kGB)
+    int64_t node0;  // first node in the GNode array
+};
 template <typename T>
-void launch_gather(const Task* tasks, int ntask, int64_t max_win, const SubDesc* subs,
-                   const Incoming* inc, const DevProblem& P, const T* m, const cplx<T>* an,
-                   const cplx<T>* af, const T* beta_tab, const cplx<double>* b, int nrhs,
-                   const cplx<T>* buf, cplx<T>* bsrc, int64_t buf_rhs_stride, int max_line, int max_lines,
-                   cudaStream_t st);  // reads the senders' solutions in buf, writes sources into bsrc
+void launch_gather(const GBlock* blocks, int nblocks, const GNode* nodes, const Task* tasks,
+                   const SubDesc* subs, const Incoming* inc, const DevProblem& P, const T* m,
+                   const cplx<T>* an, const cplx<T>* af, const T* beta_tab, const cplx<double>* b, int nrhs,
+                   const cplx<T>* buf, cplx<T>* bsrc, int64_t rstride, cudaStream_t st);
 
 template <typename T>
 void launch_assemble(const DevProblem& P, const SubDesc* subs, const int* box_of,
@@ -230,9 +246,10 @@ void launch_assemble(const DevProblem& P, const SubDesc* subs, const int* box_of
 // global FP64 kernels
 void launch_scale_J(const DevProblem& P, const Win<double>& g, const cplx<double>* f,
                     cplx<double>* b, int nrhs, bool conj_in, cudaStream_t st);
-void launch_apply_A(const DevProblem& P, const Win<double>& g, const double* m,
-                    const cplx<double>* b, const cplx<double>* u, cplx<double>* r, int nrhs,
-                    cudaStream_t st);  // r = b - A u (b may be null: r = -A u)
+void launch_stencil_ff(const DevProblem& P, const Win<double>& g, const double* m, float4* stc,
+                       cudaStream_t st);
+void launch_apply_A(const DevProblem& P, const float4* stc, const cplx<double>* b, const cplx<double>* u,
+                    cplx<double>* r, int nrhs, cudaStream_t st);  // r = b - A u (b may be null: r = -A u)
 void launch_dots(const cplx<double>* V, int64_t vstride, int nv, const cplx<double>* w,
                  int64_t n, int nrhs, cplx<double>* out, cplx<double>* partial, int nblk,
                  cudaStream_t st);  // out[i*nrhs+c] = <V_i[c], w[c]>

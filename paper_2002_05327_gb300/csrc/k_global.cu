@@ -51,45 +51,75 @@ void launch_scale_J(const DevProblem& P, const Win<double>& g, const cplx<double
     scale_J_kernel<<<grid, 256, 0, st>>>(P, g, f, b, nrhs, conj_in ? 1 : 0);
 }
 
-// One thread per grid node: the stencil (FP64 complex reciprocals) is formed
-// once, split into float-float, and applied to every right-hand side in
-// float-float arithmetic on the FP32 pipes (vectors stay FP64 in memory).
-// Outside the PML every alpha is 1, so the coefficients are real (their
-// imaginary parts are exact zeros) and each term needs two products, not four.
-__global__ void apply_A_kernel(DevProblem P, Win<double> w, const double* __restrict__ m,
-                               const cplx<double>* __restrict__ b,
-                               const cplx<double>* __restrict__ u, cplx<double>* __restrict__ r,
-                               int nrhs) {
+// The J-multiplied stencil of every grid node (diagonal, then the +/- neighbour
+// of each axis), formed once in FP64 and stored as float-float pairs
+// (re.hi, re.lo, im.hi, im.lo): the operator product then needs no FP64
+// instruction.
+__global__ void stencil_ff_kernel(DevProblem P, Win<double> w, const double* __restrict__ m, double ih2,
+                                  double om2, float4* __restrict__ stc) {
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Ng) return;
     int g[3];
     unflat(k, P.N, g);
-    const Stencil<double> st = stencil_at(w, P.ndim, g, 1.0 / (P.h * P.h), P.omega * P.omega, m[k]);
+    const Stencil<double> st = stencil_at(w, P.ndim, g, ih2, om2, m[k]);
+    const int npt = 1 + 2 * P.ndim;
+    auto put = [&](int i, cplx<double> v) {
+        const ff r = split_d(v.re), im = split_d(v.im);
+        stc[k * npt + i] = make_float4(r.hi, r.lo, im.hi, im.lo);
+    };
+    put(0, st.diag);
+    for (int a = 0; a < P.ndim; ++a) {
+        put(1 + 2 * a, st.cp[a]);
+        put(2 + 2 * a, st.cm[a]);
+    }
+}
+
+void launch_stencil_ff(const DevProblem& P, const Win<double>& g, const double* m, float4* stc,
+                       cudaStream_t st) {
+    const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
+    stencil_ff_kernel<<<(unsigned)((Ng + 255) / 256), 256, 0, st>>>(P, g, m, 1.0 / (P.h * P.h),
+                                                                     P.omega * P.omega, stc);
+}
+
+// b - A u (or -A u without b), one thread per grid node: the node's stencil
+// (float-float, from stencil_ff_kernel) is read once and applied to every
+// right-hand side in float-float arithmetic on the FP32 pipes (vectors stay
+// FP64 in memory).  Outside the PML every alpha is 1, so the coefficients are
+// real (their imaginary parts are exact zeros) and each term needs two
+// products, not four.
+__global__ void apply_A_kernel(DevProblem P, const float4* __restrict__ stc, const cplx<double>* __restrict__ b,
+                               const cplx<double>* __restrict__ u, cplx<double>* __restrict__ r, int nrhs) {
+    const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= Ng) return;
+    int g[3];
+    unflat(k, P.N, g);
+    const int npt = 1 + 2 * P.ndim;
+    const float4* sk = stc + k * npt;
     int64_t off[6];
-    cplx<double> co[6];
+    ff cr[6], ci[6];
     int np = 0;
     int64_t stride = 1;
     for (int a = 0; a < P.ndim; ++a) {
         if (g[a] + 1 < P.N[a]) {
+            const float4 q = sk[1 + 2 * a];
             off[np] = stride;
-            co[np++] = st.cp[a];
+            cr[np] = {q.x, q.y};
+            ci[np++] = {q.z, q.w};
         }
         if (g[a] > 0) {
+            const float4 q = sk[2 + 2 * a];
             off[np] = -stride;
-            co[np++] = st.cm[a];
+            cr[np] = {q.x, q.y};
+            ci[np++] = {q.z, q.w};
         }
         stride *= P.N[a];
     }
-    bool real = st.diag.im == 0.0;
-    for (int i = 0; i < np; ++i) real = real && co[i].im == 0.0;
-    const ff dr = split_d(st.diag.re), di = split_d(st.diag.im);
-    ff cr[6], ci[6];
-#pragma unroll
-    for (int i = 0; i < 6; ++i) {
-        cr[i] = i < np ? split_d(co[i].re) : ff{0.f, 0.f};
-        ci[i] = i < np ? split_d(co[i].im) : ff{0.f, 0.f};
-    }
+    const float4 q0 = sk[0];
+    const ff dr = {q0.x, q0.y}, di = {q0.z, q0.w};
+    bool real = di.hi == 0.f;
+    for (int i = 0; i < np; ++i) real = real && ci[i].hi == 0.f;
     for (int c = 0; c < nrhs; ++c) {
         const cplx<double>* uc = u + (int64_t)c * Ng + k;
         // -(A u) accumulated, then + b
@@ -123,11 +153,10 @@ __global__ void apply_A_kernel(DevProblem P, Win<double> w, const double* __rest
     }
 }
 
-void launch_apply_A(const DevProblem& P, const Win<double>& g, const double* m,
-                    const cplx<double>* b, const cplx<double>* u, cplx<double>* r, int nrhs,
-                    cudaStream_t st) {
+void launch_apply_A(const DevProblem& P, const float4* stc, const cplx<double>* b, const cplx<double>* u,
+                    cplx<double>* r, int nrhs, cudaStream_t st) {
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
-    apply_A_kernel<<<(unsigned)((Ng + 255) / 256), 256, 0, st>>>(P, g, m, b, u, r, nrhs);
+    apply_A_kernel<<<(unsigned)((Ng + 255) / 256), 256, 0, st>>>(P, stc, b, u, r, nrhs);
 }
 
 // ---- batched dots: out[i*nrhs + c] = sum_k conj(V_i[c][k]) w[c][k]

@@ -31,15 +31,27 @@ __device__ __forceinline__ T beta1(int dir, int k, int blo, int bhi, int d, cons
 constexpr int kMaxIncoming = 32;  // routing gives at most 8 (2D) / 26 (3D); the host checks
 constexpr int kRG = 8;             // right-hand sides per thread
 
-// Block = one line of the window (fixed y, z) x a span of x; the incoming
-// transfers whose strip can meet this line are selected once per block into
-// shared memory, so a thread only tests its x.  Each thread handles kRG
-// right-hand sides with independent loads.
 template <typename T>
-__global__ void __launch_bounds__(128) gather_kernel(const Task* __restrict__ tasks,
+__device__ __forceinline__ cplx<T> src_cast(cplx<double> v) {
+    if constexpr (sizeof(T) == 4)
+        return mk<float>(ffa::d2f(v.re), ffa::d2f(v.im));  // off the FP64 pipe
+    else
+        return v;
+}
+
+// Block = up to kGB consecutive nodes of one task's work list (GNode: the
+// window nodes the first sweep's box or an incoming strip reaches, with the
+// incoming transfers that reach each), so every thread has a node to write.
+// The task's incoming transfers are staged in shared memory; each thread
+// handles kRG right-hand sides with independent loads and sums the transfers
+// in the order of the incoming list.
+template <typename T>
+__global__ void __launch_bounds__(kGB) gather_kernel(const GBlock* __restrict__ blocks,
+                                                     const GNode* __restrict__ nodes,
+                                                     const Task* __restrict__ tasks,
                                                      const SubDesc* __restrict__ subs,
-                                                     const Incoming* __restrict__ inc, DevProblem P,
-                                                     const T* __restrict__ m,
+                                                     const Incoming* __restrict__ inc, DevProblem P, T ih2,
+                                                     T omega2, const T* __restrict__ m,
                                                      const cplx<T>* __restrict__ an,
                                                      const cplx<T>* __restrict__ af,
                                                      const T* __restrict__ tab,
@@ -53,31 +65,17 @@ __global__ void __launch_bounds__(128) gather_kernel(const Task* __restrict__ ta
         int64_t off;         // sender buffer offset
     };
     __shared__ InS sin[kMaxIncoming];
-    __shared__ int sel[kMaxIncoming];
-    __shared__ int keep[kMaxIncoming];
-    __shared__ int nsel;
     __shared__ T stab[129];
-    const Task tk = tasks[blockIdx.y];
+    const GBlock gb = blocks[blockIdx.x];
+    const bool act = (int)threadIdx.x < gb.cnt;
+    const GNode nd = act ? nodes[gb.node0 + threadIdx.x] : GNode{0u, 0u};
+    const Task tk = tasks[gb.task];
     const SubDesc& S = subs[tk.sub];
-    const int ndim = P.ndim;
-    const int spans = (S.nw[0] + blockDim.x - 1) / blockDim.x;
-    const int line = blockIdx.x / spans;
-    if (line >= S.nw[1] * S.nw[2]) return;
-    const int xspan = blockIdx.x % spans;
-    int g[3];
-    g[1] = S.lo[1] + line % S.nw[1];
-    g[2] = S.lo[2] + line / S.nw[1];
-    // each thread stages one incoming transfer and tests its strip on y (and z)
     const int ni = tk.in_cnt;
     if ((int)threadIdx.x < ni) {
         const int i = threadIdx.x;
         const Incoming I = inc[tk.in_off + i];
         const SubDesc& R = subs[I.sender];
-        bool in = true;
-        for (int a = 1; a < ndim; ++a) {
-            if (I.dir[a] > 0) in &= (g[a] >= R.box_hi[a]) && (g[a] <= R.box_hi[a] + P.d);
-            if (I.dir[a] < 0) in &= (g[a] < R.box_lo[a]) && (g[a] >= R.box_lo[a] - 1 - P.d);
-        }
         for (int a = 0; a < 3; ++a) {
             sin[i].dir[a] = I.dir[a];
             sin[i].blo[a] = R.box_lo[a];
@@ -86,113 +84,93 @@ __global__ void __launch_bounds__(128) gather_kernel(const Task* __restrict__ ta
             sin[i].nw[a] = R.nw[a];
         }
         sin[i].off = I.sender_buf_off;
-        keep[i] = in;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {  // ordered compaction keeps the summation order fixed
-        int ns = 0;
-        for (int i = 0; i < ni; ++i)
-            if (keep[i]) sel[ns++] = i;
-        nsel = ns;
     }
     for (int i = threadIdx.x; i <= P.d; i += blockDim.x) stab[i] = tab[i];
     __syncthreads();
-    // only the sweep-0 box and the strips of the incoming transfers are ever
-    // written (the rest of bsrc stays zero): a line no strip meets has nothing
-    if (tk.sweep != 0 && nsel == 0) return;
-    const int x0 = xspan * blockDim.x + threadIdx.x;
-    if (x0 >= S.nw[0]) return;
-    g[0] = S.lo[0] + x0;
-    const int x[3] = {x0, g[1] - S.lo[1], g[2] - S.lo[2]};
-    const int64_t k = ((int64_t)x[2] * S.nw[1] + x[1]) * S.nw[0] + x0;
+    if (!act) return;
+    const int ndim = P.ndim;
+    const int64_t k = nd.k;
+    int x[3];
+    x[0] = (int)(k % S.nw[0]);
+    x[1] = (int)((k / S.nw[0]) % S.nw[1]);
+    x[2] = (int)(k / ((int64_t)S.nw[0] * S.nw[1]));
+    int g[3];
+    for (int a = 0; a < 3; ++a) g[a] = S.lo[a] + x[a];
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
     const int64_t gidx = ((int64_t)g[2] * P.N[1] + g[1]) * P.N[0] + g[0];
-    const int c0 = blockIdx.z * kRG;
+    const int c0 = blockIdx.y * kRG;
     const int nc = min(kRG, nrhs - c0);
     cplx<T>* __restrict__ out = bsrc + tk.buf_off + k + (int64_t)c0 * rstride;
     const cplx<T>* __restrict__ src = buf;  // sender solutions
 
-    bool inbox = tk.sweep == 0;
-    for (int a = 0; a < ndim; ++a) inbox &= (g[a] >= S.box_lo[a]) && (g[a] < S.box_hi[a]);
+    const bool inbox = (nd.mask >> 31) != 0u;
     cplx<T> val[kRG];
 #pragma unroll
     for (int c = 0; c < kRG; ++c)
-        val[c] = (inbox && c < nc) ? ccast<T>(b[(int64_t)(c0 + c) * Ng + gidx]) : mk<T>(0, 0);
+        val[c] = (inbox && c < nc) ? src_cast<T>(b[(int64_t)(c0 + c) * Ng + gidx]) : mk<T>(0, 0);
 
-    bool have_st = false;
-    bool touched = inbox;  // the node belongs to the fixed set of written nodes
-    cplx<T> coef[7];
-    const int npt = 1 + 2 * ndim;
-    const int ns = nsel;
-    for (int ii = 0; ii < ns; ++ii) {
-        const InS& R = sin[sel[ii]];
-        const int dd0 = R.dir[0];
-        bool in = true;
-        if (dd0 > 0) in = (g[0] >= R.bhi[0]) && (g[0] <= R.bhi[0] + P.d);
-        if (dd0 < 0) in = (g[0] < R.blo[0]) && (g[0] >= R.blo[0] - 1 - P.d);
-        if (!in) continue;
-        touched = true;
-        if (!have_st) {
-            Win<T> w;
-            for (int a = 0; a < 3; ++a) {
-                w.lo[a] = S.lo[a];
-                w.n[a] = S.nw[a];
-                w.alpha_node[a] = an + S.alpha_off[a];
-                w.alpha_face[a] = af + S.face_off[a];
-            }
-            const Stencil<T> st =
-                stencil_at(w, ndim, x, T(1.0 / (P.h * P.h)), T(P.omega * P.omega), m[gidx]);
-            coef[0] = st.diag;
-            for (int a = 0; a < 3; ++a) {
-                coef[1 + 2 * a] = st.cp[a];
-                coef[2 + 2 * a] = st.cm[a];
-            }
-            have_st = true;
+    unsigned int todo = nd.mask & 0x7FFFFFFFu;
+    if (todo) {
+        Win<T> w;
+        for (int a = 0; a < 3; ++a) {
+            w.lo[a] = S.lo[a];
+            w.n[a] = S.nw[a];
+            w.alpha_node[a] = an + S.alpha_off[a];
+            w.alpha_face[a] = af + S.face_off[a];
         }
-        for (int pt = 0; pt < npt; ++pt) {
-            int gg[3] = {g[0], g[1], g[2]};
-            bool ok = true;
-            if (pt > 0) {
-                const int ax = (pt - 1) / 2, o = (pt & 1) ? 1 : -1;
-                gg[ax] += o;
-                const int xl = gg[ax] - S.lo[ax];
-                ok = xl >= 0 && xl < S.nw[ax];  // Dirichlet outside the receiver window
-            }
-            T beta = T(1);
-            int64_t li = 0;
-            for (int a = ndim - 1; a >= 0 && ok; --a) {
-                const int xl = gg[a] - R.lo[a];
-                if (xl < 0 || xl >= R.nw[a]) ok = false;  // zero outside the sender window
-                li = li * R.nw[a] + xl;
-                const int dd = R.dir[a];
-                if (dd > 0 && gg[a] >= R.bhi[a]) beta *= stab[min(gg[a] - R.bhi[a], P.d)];
-                if (dd < 0 && gg[a] < R.blo[a]) beta *= stab[min(R.blo[a] - 1 - gg[a], P.d)];
-            }
-            if (!ok || beta == T(0)) continue;
-            const cplx<T> cw = beta * coef[pt];
-            const cplx<T>* sp = src + R.off + li + (int64_t)c0 * rstride;
+        const Stencil<T> st = stencil_at(w, ndim, x, ih2, omega2, m[gidx]);
+        cplx<T> coef[7];
+        coef[0] = st.diag;
+        for (int a = 0; a < 3; ++a) {
+            coef[1 + 2 * a] = st.cp[a];
+            coef[2 + 2 * a] = st.cm[a];
+        }
+        const int npt = 1 + 2 * ndim;
+        while (todo) {  // incoming transfers reaching this node, in list order
+            const InS& R = sin[__ffs(todo) - 1];
+            todo &= todo - 1;
+            for (int pt = 0; pt < npt; ++pt) {
+                int gg[3] = {g[0], g[1], g[2]};
+                bool ok = true;
+                if (pt > 0) {
+                    const int ax = (pt - 1) / 2, o = (pt & 1) ? 1 : -1;
+                    gg[ax] += o;
+                    const int xl = gg[ax] - S.lo[ax];
+                    ok = xl >= 0 && xl < S.nw[ax];  // Dirichlet outside the receiver window
+                }
+                T beta = T(1);
+                int64_t li = 0;
+                for (int a = ndim - 1; a >= 0 && ok; --a) {
+                    const int xl = gg[a] - R.lo[a];
+                    if (xl < 0 || xl >= R.nw[a]) ok = false;  // zero outside the sender window
+                    li = li * R.nw[a] + xl;
+                    const int dd = R.dir[a];
+                    if (dd > 0 && gg[a] >= R.bhi[a]) beta *= stab[min(gg[a] - R.bhi[a], P.d)];
+                    if (dd < 0 && gg[a] < R.blo[a]) beta *= stab[min(R.blo[a] - 1 - gg[a], P.d)];
+                }
+                if (!ok || beta == T(0)) continue;
+                const cplx<T> cw = beta * coef[pt];
+                const cplx<T>* sp = src + R.off + li + (int64_t)c0 * rstride;
 #pragma unroll
-            for (int c = 0; c < kRG; ++c)
-                if (c < nc) val[c] = val[c] - cw * sp[(int64_t)c * rstride];
+                for (int c = 0; c < kRG; ++c)
+                    if (c < nc) val[c] = val[c] - cw * sp[(int64_t)c * rstride];
+            }
         }
     }
-    if (!touched) return;
 #pragma unroll
     for (int c = 0; c < kRG; ++c)
         if (c < nc) out[(int64_t)c * rstride] = val[c];
 }
 
 template <typename T>
-void launch_gather(const Task* tasks, int ntask, int64_t max_win, const SubDesc* subs,
-                   const Incoming* inc, const DevProblem& P, const T* m, const cplx<T>* an,
-                   const cplx<T>* af, const T* beta_tab, const cplx<double>* b, int nrhs,
-                   const cplx<T>* buf, cplx<T>* bsrc, int64_t rstride, int max_line, int max_lines,
-                   cudaStream_t st) {
-    if (ntask == 0) return;
-    const int nt = 128;
-    const int spans = (max_line + nt - 1) / nt;
-    dim3 grid((unsigned)(spans * max_lines), ntask, (nrhs + kRG - 1) / kRG);
-    gather_kernel<T><<<grid, nt, 0, st>>>(tasks, subs, inc, P, m, an, af, beta_tab, b, nrhs, buf, bsrc,
+void launch_gather(const GBlock* blocks, int nblocks, const GNode* nodes, const Task* tasks,
+                   const SubDesc* subs, const Incoming* inc, const DevProblem& P, const T* m,
+                   const cplx<T>* an, const cplx<T>* af, const T* beta_tab, const cplx<double>* b, int nrhs,
+                   const cplx<T>* buf, cplx<T>* bsrc, int64_t rstride, cudaStream_t st) {
+    if (nblocks == 0) return;
+    dim3 grid((unsigned)nblocks, (nrhs + kRG - 1) / kRG);
+    gather_kernel<T><<<grid, kGB, 0, st>>>(blocks, nodes, tasks, subs, inc, P, T(1.0 / (P.h * P.h)),
+                                           T(P.omega * P.omega), m, an, af, beta_tab, b, nrhs, buf, bsrc,
                                            rstride);
 }
 
@@ -341,14 +319,14 @@ void launch_assemble(const DevProblem& P, const SubDesc* subs, const int* box_of
                                             U);
 }
 
-template void launch_gather<float>(const Task*, int, int64_t, const SubDesc*, const Incoming*,
-                                   const DevProblem&, const float*, const cplx<float>*,
+template void launch_gather<float>(const GBlock*, int, const GNode*, const Task*, const SubDesc*,
+                                   const Incoming*, const DevProblem&, const float*, const cplx<float>*,
                                    const cplx<float>*, const float*, const cplx<double>*, int,
-                                   const cplx<float>*, cplx<float>*, int64_t, int, int, cudaStream_t);
-template void launch_gather<double>(const Task*, int, int64_t, const SubDesc*, const Incoming*,
-                                    const DevProblem&, const double*, const cplx<double>*,
+                                   const cplx<float>*, cplx<float>*, int64_t, cudaStream_t);
+template void launch_gather<double>(const GBlock*, int, const GNode*, const Task*, const SubDesc*,
+                                    const Incoming*, const DevProblem&, const double*, const cplx<double>*,
                                     const cplx<double>*, const double*, const cplx<double>*, int,
-                                    const cplx<double>*, cplx<double>*, int64_t, int, int, cudaStream_t);
+                                    const cplx<double>*, cplx<double>*, int64_t, cudaStream_t);
 template void launch_assemble<float>(const DevProblem&, const SubDesc*, const int*,
                                      const int64_t*, int, const float*, const cplx<float>*,
                                      int64_t, int, cplx<double>*, cudaStream_t);

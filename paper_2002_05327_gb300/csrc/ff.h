@@ -7,6 +7,8 @@
 
 #include <cstdint>
 
+#include "helm_internal.h"
+
 namespace helm {
 namespace ffa {
 
@@ -103,6 +105,33 @@ __device__ __forceinline__ ff ff_sum(ff a, ff b) {
 }
 __device__ __forceinline__ ff shfl_down_ff(ff a, int o) {
     return {__shfl_down_sync(0xffffffffu, a.hi, o), __shfl_down_sync(0xffffffffu, a.lo, o)};
+}
+
+// ---- complex vectors of the FP64 solver in two storage forms: complex128
+// (the caller's arrays) and float-float (one float4 per entry: re.hi, re.lo,
+// im.hi, im.lo; the Krylov work vectors), read and written as pairs of ff
+struct cff {
+    ff re, im;
+};
+__device__ __forceinline__ cff ld_c(const cplx<double>* p) {
+    const cplx<double> v = *p;
+    return {split_d(v.re), split_d(v.im)};
+}
+__device__ __forceinline__ cff ld_c(const float4* p) {
+    const float4 v = *p;
+    return {{v.x, v.y}, {v.z, v.w}};
+}
+// hi + lo renormalised (TwoSum): |lo| <= half a unit of hi, so that a later
+// product may drop lo * lo
+__device__ __forceinline__ ff ff_norm(ff a) {
+    const float s = a.hi + a.lo;
+    const float v = s - a.hi;
+    return {s, (a.hi - (s - v)) + (a.lo - v)};
+}
+__device__ __forceinline__ void st_c(cplx<double>* p, cff v) { *p = mk<double>(join_d(v.re), join_d(v.im)); }
+__device__ __forceinline__ void st_c(float4* p, cff v) {
+    const ff r = ff_norm(v.re), i = ff_norm(v.im);
+    *p = make_float4(r.hi, r.lo, i.hi, i.lo);
 }
 
 }  // namespace ffa

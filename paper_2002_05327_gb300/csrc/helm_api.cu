@@ -166,10 +166,10 @@ struct helm_ctx {
     void* buf = nullptr;           // window buffers, complex T, [rhs][nodes][window]
     cplx<double>* bvec = nullptr;  // J-scaled source of one DDM application
     int cap_vec_rhs = 0;
-    std::vector<cplx<double>*> gm;  // GMRES vectors (each nrhs*Ng)
+    std::vector<cplx<double>*> gm;  // GMRES vectors (each nrhs*Ng entries of 16 bytes; float-float)
     int gm_rhs = 0;
-    cplx<double>** vptr_d = nullptr;  // device copies of the V_i and Z_i pointers
-    cplx<double>** zptr_d = nullptr;
+    float4** vptr_d = nullptr;  // device copies of the V_i and Z_i pointers
+    float4** zptr_d = nullptr;
     cplx<double>* small_d = nullptr;  // dots / coefficients
     cplx<double>* partial_d = nullptr;
     double* scal_d = nullptr;
@@ -777,8 +777,10 @@ int auto_panel(const helm_ctx* c, int nrhs) {
 }
 
 // One application of Algorithm 3.1 / 4.1 to the J-scaled source b (device,
-// complex128 [nrhs][grid]); the assembled u_DDM goes to U (device).
-int apply_ddm_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* U) {
+// [nrhs][grid], complex128 or float-float); the assembled u_DDM goes to U
+// (device, the same form).
+template <typename VB>
+int apply_ddm_dev(helm_ctx* c, int nrhs, const VB* b, VB* U) {
     if (!c->factored) return fail(HELM_ERR_NOT_FACTORED, "call helm_factor first");
     TRY(ensure_buffers(c, nrhs));
     const int64_t rs = c->buf_per_rhs;
@@ -921,13 +923,15 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
     TRY(ensure_gm(c, nrhs, 2));
     TRY(ensure_small(c, (size_t)(m + 2) * nrhs));
     const int nblk = (int)std::min<int64_t>(256, (Ng + 4095) / 4096);
-    cplx<double>* w = c->gm[0];
-    auto V = [&](int i) { return c->gm[1 + 2 * i]; };
-    auto Z = [&](int i) { return c->gm[2 + 2 * i]; };
+    // work vectors in float-float form (one float4 per complex entry)
+    auto fv = [&](int i) { return reinterpret_cast<float4*>(c->gm[i]); };
+    float4* w = fv(0);
+    auto V = [&](int i) { return fv(1 + 2 * i); };
+    auto Z = [&](int i) { return fv(2 + 2 * i); };
     std::vector<double> bn(nrhs), res(nrhs, 1.0);
     std::vector<cplx<double>> hd((size_t)(m + 2) * nrhs);
     std::vector<double> sc(nrhs);
-    auto norms = [&](const cplx<double>* v, std::vector<double>& out) -> int {
+    auto norms = [&](const auto* v, std::vector<double>& out) -> int {
         { ProfScope ps_(c, HELM_K_KRYLOV, 2); launch_norms2(v, Ng, nrhs, c->small_d, c->partial_d, nblk, c->stream); }
         CK(cudaMemcpyAsync(hd.data(), c->small_d, nrhs * 16, cudaMemcpyDeviceToHost, c->stream));
         CK(cudaStreamSynchronize(c->stream));
@@ -973,7 +977,7 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
         int k = 0;
         for (; k < m && total < maxit; ++k) {
             TRY(ensure_gm(c, nrhs, 2 * k + 4));  // Z_k and V_{k+1}
-            w = c->gm[0];
+            w = fv(0);
             TRY(apply_ddm_dev(c, nrhs, V(k), Z(k)));
             ++apps;
             // w = -A z_k (apply_A with no b); CGS2 on w: h = V^H w, w -= V h, twice.
@@ -984,7 +988,7 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
             }
             std::vector<std::vector<cd>> hsum(nrhs, std::vector<cd>(k + 2, 0.0));
             {
-                std::vector<cplx<double>*> vp(k + 1);
+                std::vector<float4*> vp(k + 1);
                 for (int i = 0; i <= k; ++i) vp[i] = V(i);
                 CK(cudaMemcpyAsync(c->vptr_d, vp.data(), vp.size() * sizeof(void*),
                                    cudaMemcpyHostToDevice, c->stream));
@@ -1060,7 +1064,7 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
         CK(cudaMemcpyAsync(c->small_d, coef.data(), coef.size() * 16, cudaMemcpyHostToDevice,
                            c->stream));
         if (k > 0) {
-            std::vector<cplx<double>*> zp(k);
+            std::vector<float4*> zp(k);
             for (int i = 0; i < k; ++i) zp[i] = Z(i);
             CK(cudaMemcpyAsync(c->zptr_d, zp.data(), zp.size() * sizeof(void*),
                                cudaMemcpyHostToDevice, c->stream));

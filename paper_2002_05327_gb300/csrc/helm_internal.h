@@ -231,16 +231,16 @@ struct GBlock {
     int cnt;        // nodes (<= kGB)
     int64_t node0;  // first node in the GNode array
 };
-template <typename T>
+template <typename T, typename VB>
 void launch_gather(const GBlock* blocks, int nblocks, const GNode* nodes, const Task* tasks,
                    const SubDesc* subs, const Incoming* inc, const DevProblem& P, const T* m,
-                   const cplx<T>* an, const cplx<T>* af, const T* beta_tab, const cplx<double>* b, int nrhs,
+                   const cplx<T>* an, const cplx<T>* af, const T* beta_tab, const VB* b, int nrhs,
                    const cplx<T>* buf, cplx<T>* bsrc, int64_t rstride, cudaStream_t st);
 
-template <typename T>
-void launch_assemble(const DevProblem& P, const SubDesc* subs, const int* box_of,
-                     const int64_t* node_buf, int nsweeps, const T* beta_tab,
-                     const cplx<T>* buf, int64_t buf_rhs_stride, int nrhs, cplx<double>* U,
+// u_DDM into U: complex128, or float-float (float4 per entry) for the Krylov work vectors
+template <typename T, typename VU>
+void launch_assemble(const DevProblem& P, const SubDesc* subs, const int* box_of, const int64_t* node_buf,
+                     int nsweeps, const T* beta_tab, const cplx<T>* buf, int64_t rstride, int nrhs, VU* U,
                      cudaStream_t st);
 
 // global FP64 kernels
@@ -248,23 +248,25 @@ void launch_scale_J(const DevProblem& P, const Win<double>& g, const cplx<double
                     cplx<double>* b, int nrhs, bool conj_in, cudaStream_t st);
 void launch_stencil_ff(const DevProblem& P, const Win<double>& g, const double* m, float4* stc,
                        cudaStream_t st);
-void launch_apply_A(const DevProblem& P, const float4* stc, const cplx<double>* b, const cplx<double>* u,
-                    cplx<double>* r, int nrhs, cudaStream_t st);  // r = b - A u (b may be null: r = -A u)
-void launch_dots(const cplx<double>* V, int64_t vstride, int nv, const cplx<double>* w,
-                 int64_t n, int nrhs, cplx<double>* out, cplx<double>* partial, int nblk,
-                 cudaStream_t st);  // out[i*nrhs+c] = <V_i[c], w[c]>
-void launch_sub_combo(cplx<double>* w, const cplx<double>* V, int64_t vstride, int nv,
-                      const cplx<double>* coef, int64_t n, int nrhs, double sign,
-                      cudaStream_t st);  // w[c] += sign * sum_i coef[i*nrhs+c] V_i[c]
-void launch_norms2(const cplx<double>* v, int64_t n, int nrhs, cplx<double>* out,
-                   cplx<double>* partial, int nblk, cudaStream_t st);  // out[c] = |v[c]|^2
-// fused over nv vectors given as a device array of pointers (nv <= 64)
-void launch_mdots(const cplx<double>* const* V, int nv, const cplx<double>* w, int64_t n, int nrhs,
-                  cplx<double>* out, cplx<double>* partial, int nblk, cudaStream_t st);
-void launch_mcombo(cplx<double>* w, const cplx<double>* const* V, int nv, const cplx<double>* coef,
-                   int64_t n, int nrhs, double sign, cudaStream_t st);
-void launch_scale_vec(cplx<double>* v, const cplx<double>* src, const double* s, int64_t n,
-                      int nrhs, cudaStream_t st);  // v[c] = src[c] * s[c]
+// The GMRES work vectors (w, V_i, Z_i) are float-float, one float4 (re.hi,
+// re.lo, im.hi, im.lo) per complex entry, so the Krylov kernels neither split
+// nor join doubles; the caller's complex128 arrays (b, x) are split on load
+// and joined on store.
+// r = b - A u (b may be null: r = -A u); u, r complex128 or float-float
+template <typename VU, typename VR>
+void launch_apply_A(const DevProblem& P, const float4* stc, const cplx<double>* b, const VU* u, VR* r, int nrhs,
+                    cudaStream_t st);
+template <typename VV>
+void launch_norms2(const VV* v, int64_t n, int nrhs, cplx<double>* out, cplx<double>* partial, int nblk,
+                   cudaStream_t st);  // out[c] = |v[c]|^2
+// fused over nv float-float vectors given as a device array of pointers (nv <= 64)
+void launch_mdots(const float4* const* V, int nv, const float4* w, int64_t n, int nrhs, cplx<double>* out,
+                  cplx<double>* partial, int nblk, cudaStream_t st);  // out[i*nrhs+c] = <V_i[c], w[c]>
+template <typename VW>
+void launch_mcombo(VW* w, const float4* const* V, int nv, const cplx<double>* coef, int64_t n, int nrhs,
+                   double sign, cudaStream_t st);  // w[c] += sign * sum_i coef[i*nrhs+c] V_i[c]
+void launch_scale_vec(float4* v, const float4* src, const double* s, int64_t n, int nrhs,
+                      cudaStream_t st);  // v[c] = src[c] * s[c]
 void launch_conj(cplx<double>* v, int64_t count, cudaStream_t st);
 void launch_gradient(const DevProblem& P, const Win<double>& g, const cplx<double>* U,
                      const cplx<double>* L, int nsrc, double* grad, cudaStream_t st);

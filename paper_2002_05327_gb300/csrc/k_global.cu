@@ -82,115 +82,103 @@ void launch_stencil_ff(const DevProblem& P, const Win<double>& g, const double* 
                                                                      P.omega * P.omega, stc);
 }
 
-// b - A u (or -A u without b), one thread per grid node: the node's stencil
-// (float-float, from stencil_ff_kernel) is read once and applied to every
-// right-hand side in float-float arithmetic on the FP32 pipes (vectors stay
-// FP64 in memory).  Outside the PML every alpha is 1, so the coefficients are
-// real (their imaginary parts are exact zeros) and each term needs two
-// products, not four.
+// b - A u (or -A u without b).  One thread per (grid node, pair of
+// right-hand sides): the node's stencil (float-float, from stencil_ff_kernel)
+// is read once and applied to both in float-float arithmetic on the FP32
+// pipes, their loads issued together.  u and r are complex128 (the caller's
+// arrays) or float-float (the Krylov work vectors).  Outside the PML every
+// alpha is 1, so the coefficients are real (their imaginary parts are exact
+// zeros) and each term needs two products, not four.
+constexpr int kAR = 2;  // right-hand sides per thread of the operator product
+template <typename VU, typename VR>
 __global__ void apply_A_kernel(DevProblem P, const float4* __restrict__ stc, const cplx<double>* __restrict__ b,
-                               const cplx<double>* __restrict__ u, cplx<double>* __restrict__ r, int nrhs) {
+                               const VU* __restrict__ u, VR* __restrict__ r, int nrhs) {
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Ng) return;
+    const int c0 = blockIdx.y * kAR;
     int g[3];
     unflat(k, P.N, g);
     const int npt = 1 + 2 * P.ndim;
     const float4* sk = stc + k * npt;
+    // neighbour slots 2a (+1 along axis a) and 2a+1 (-1), fixed so that the
+    // arrays stay in registers; a slot off the grid (Dirichlet) is skipped
     int64_t off[6];
+    bool have[6];
     ff cr[6], ci[6];
-    int np = 0;
     int64_t stride = 1;
-    for (int a = 0; a < P.ndim; ++a) {
-        if (g[a] + 1 < P.N[a]) {
-            const float4 q = sk[1 + 2 * a];
-            off[np] = stride;
-            cr[np] = {q.x, q.y};
-            ci[np++] = {q.z, q.w};
-        }
-        if (g[a] > 0) {
-            const float4 q = sk[2 + 2 * a];
-            off[np] = -stride;
-            cr[np] = {q.x, q.y};
-            ci[np++] = {q.z, q.w};
-        }
-        stride *= P.N[a];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const bool on = a < P.ndim;
+        have[2 * a] = on && g[a] + 1 < P.N[a];
+        have[2 * a + 1] = on && g[a] > 0;
+        off[2 * a] = stride;
+        off[2 * a + 1] = -stride;
+        const float4 qp = have[2 * a] ? sk[1 + 2 * a] : make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 qm = have[2 * a + 1] ? sk[2 + 2 * a] : make_float4(0.f, 0.f, 0.f, 0.f);
+        cr[2 * a] = {qp.x, qp.y};
+        ci[2 * a] = {qp.z, qp.w};
+        cr[2 * a + 1] = {qm.x, qm.y};
+        ci[2 * a + 1] = {qm.z, qm.w};
+        if (on) stride *= P.N[a];
     }
     const float4 q0 = sk[0];
     const ff dr = {q0.x, q0.y}, di = {q0.z, q0.w};
     bool real = di.hi == 0.f;
-    for (int i = 0; i < np; ++i) real = real && ci[i].hi == 0.f;
-    for (int c = 0; c < nrhs; ++c) {
-        const cplx<double>* uc = u + (int64_t)c * Ng + k;
-        // -(A u) accumulated, then + b
-        ff ar = {0.f, 0.f}, ai = {0.f, 0.f};
-        if (b) {
-            const cplx<double> bv = b[(int64_t)c * Ng + k];
-            ar = split_d(bv.re);
-            ai = split_d(bv.im);
-        }
-        const cplx<double> u0 = uc[0];
-        const ff ur = split_d(u0.re), ui = split_d(u0.im);
-        acc_mul(ar, ff_neg(dr), ur);
-        acc_mul(ai, ff_neg(dr), ui);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) real = real && ci[i].hi == 0.f;
+    // loads of both right-hand sides first
+    cff u0[kAR], un[kAR][6], bv[kAR];
+#pragma unroll
+    for (int j = 0; j < kAR; ++j) {
+        const int c = c0 + j < nrhs ? c0 + j : c0;
+        const VU* uc = u + (int64_t)c * Ng + k;
+        u0[j] = ld_c(uc);
+#pragma unroll
+        for (int i = 0; i < 6; ++i) un[j][i] = have[i] ? ld_c(uc + off[i]) : cff{{0.f, 0.f}, {0.f, 0.f}};
+        bv[j] = b ? ld_c(b + (int64_t)c * Ng + k) : cff{{0.f, 0.f}, {0.f, 0.f}};
+    }
+#pragma unroll
+    for (int j = 0; j < kAR; ++j) {
+        if (c0 + j >= nrhs) break;
+        // -(A u) accumulated onto b
+        ff ar = bv[j].re, ai = bv[j].im;
+        acc_mul(ar, ff_neg(dr), u0[j].re);
+        acc_mul(ai, ff_neg(dr), u0[j].im);
         if (!real) {
-            acc_mul(ar, di, ui);
-            acc_mul(ai, ff_neg(di), ur);
+            acc_mul(ar, di, u0[j].im);
+            acc_mul(ai, ff_neg(di), u0[j].re);
         }
 #pragma unroll
         for (int i = 0; i < 6; ++i) {
-            if (i >= np) break;
-            const cplx<double> un = uc[off[i]];
-            const ff nr = split_d(un.re), ni = split_d(un.im);
-            acc_mul(ar, ff_neg(cr[i]), nr);
-            acc_mul(ai, ff_neg(cr[i]), ni);
+            if (!have[i]) continue;
+            acc_mul(ar, ff_neg(cr[i]), un[j][i].re);
+            acc_mul(ai, ff_neg(cr[i]), un[j][i].im);
             if (!real) {
-                acc_mul(ar, ci[i], ni);
-                acc_mul(ai, ff_neg(ci[i]), nr);
+                acc_mul(ar, ci[i], un[j][i].im);
+                acc_mul(ai, ff_neg(ci[i]), un[j][i].re);
             }
         }
-        r[(int64_t)c * Ng + k] = mk<double>(join_d(ar), join_d(ai));
+        st_c(r + (int64_t)(c0 + j) * Ng + k, cff{ar, ai});
     }
 }
 
-void launch_apply_A(const DevProblem& P, const float4* stc, const cplx<double>* b, const cplx<double>* u,
-                    cplx<double>* r, int nrhs, cudaStream_t st) {
+template <typename VU, typename VR>
+void launch_apply_A(const DevProblem& P, const float4* stc, const cplx<double>* b, const VU* u, VR* r, int nrhs,
+                    cudaStream_t st) {
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
-    apply_A_kernel<<<(unsigned)((Ng + 255) / 256), 256, 0, st>>>(P, stc, b, u, r, nrhs);
+    dim3 grid((unsigned)((Ng + 255) / 256), (nrhs + kAR - 1) / kAR);
+    apply_A_kernel<VU, VR><<<grid, 256, 0, st>>>(P, stc, b, u, r, nrhs);
 }
+template void launch_apply_A<cplx<double>, cplx<double>>(const DevProblem&, const float4*, const cplx<double>*,
+                                                         const cplx<double>*, cplx<double>*, int, cudaStream_t);
+template void launch_apply_A<cplx<double>, float4>(const DevProblem&, const float4*, const cplx<double>*,
+                                                   const cplx<double>*, float4*, int, cudaStream_t);
+template void launch_apply_A<float4, float4>(const DevProblem&, const float4*, const cplx<double>*, const float4*,
+                                             float4*, int, cudaStream_t);
 
-// ---- batched dots: out[i*nrhs + c] = sum_k conj(V_i[c][k]) w[c][k]
+// ---- batched reductions (one Krylov space per right-hand side)
 constexpr int DOT_NT = 256;
-
-__global__ void dots_partial_kernel(const cplx<double>* __restrict__ V, int64_t vstride,
-                                    const cplx<double>* __restrict__ w, int64_t n, int nrhs,
-                                    cplx<double>* partial, int nblk) {
-    __shared__ double sr[DOT_NT], si[DOT_NT];
-    const int blk = blockIdx.x;
-    const int i = blockIdx.y / nrhs, c = blockIdx.y % nrhs;
-    const int64_t chunk = (n + nblk - 1) / nblk;
-    const int64_t k0 = (int64_t)blk * chunk;
-    const int64_t k1 = min(n, k0 + chunk);
-    const cplx<double>* vi = V + (int64_t)i * vstride + (int64_t)c * n;
-    const cplx<double>* wc = w + (int64_t)c * n;
-    double ar = 0, ai = 0;
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += DOT_NT) {
-        cplx<double> a = vi[k], b = wc[k];
-        ar += a.re * b.re + a.im * b.im;
-        ai += a.re * b.im - a.im * b.re;
-    }
-    sr[threadIdx.x] = ar;
-    si[threadIdx.x] = ai;
-    __syncthreads();
-    for (int s = DOT_NT / 2; s > 0; s >>= 1) {
-        if (threadIdx.x < s) {
-            sr[threadIdx.x] += sr[threadIdx.x + s];
-            si[threadIdx.x] += si[threadIdx.x + s];
-        }
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) partial[(int64_t)blockIdx.y * nblk + blk] = mk<double>(sr[0], si[0]);
-}
 
 __global__ void dots_final_kernel(const cplx<double>* partial, int nblk, int count,
                                   cplx<double>* out) {
@@ -204,85 +192,56 @@ __global__ void dots_final_kernel(const cplx<double>* partial, int nblk, int cou
     out[t] = mk<double>(r, i);
 }
 
-void launch_dots(const cplx<double>* V, int64_t vstride, int nv, const cplx<double>* w,
-                 int64_t n, int nrhs, cplx<double>* out, cplx<double>* partial, int nblk,
-                 cudaStream_t st) {
-    dim3 grid(nblk, nv * nrhs);
-    dots_partial_kernel<<<grid, DOT_NT, 0, st>>>(V, vstride, w, n, nrhs, partial, nblk);
-    int count = nv * nrhs;
-    dots_final_kernel<<<(count + 127) / 128, 128, 0, st>>>(partial, nblk, count, out);
-}
-
-// w[c] += sign * sum_i coef[i*nrhs+c] V_i[c]
-__global__ void sub_combo_kernel(cplx<double>* w, const cplx<double>* __restrict__ V,
-                                 int64_t vstride, int nv, const cplx<double>* __restrict__ coef,
-                                 int64_t n, int nrhs, double sign) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = blockIdx.y;
-    if (k >= n) return;
-    cplx<double> acc = w[(int64_t)c * n + k];
-    for (int i = 0; i < nv; ++i) {
-        cplx<double> a = coef[i * nrhs + c];
-        cplx<double> v = V[(int64_t)i * vstride + (int64_t)c * n + k];
-        acc = acc + sign * (a * v);
-    }
-    w[(int64_t)c * n + k] = acc;
-}
-
-void launch_sub_combo(cplx<double>* w, const cplx<double>* V, int64_t vstride, int nv,
-                      const cplx<double>* coef, int64_t n, int nrhs, double sign,
-                      cudaStream_t st) {
-    dim3 grid((unsigned)((n + 255) / 256), nrhs);
-    sub_combo_kernel<<<grid, 256, 0, st>>>(w, V, vstride, nv, coef, n, nrhs, sign);
-}
-
-__global__ void scale_vec_kernel(cplx<double>* v, const cplx<double>* src, const double* s,
+// v = s * src for a per-right-hand-side real scale s (float-float vectors)
+__global__ void scale_vec_kernel(float4* v, const float4* __restrict__ src, const double* __restrict__ s,
                                  int64_t n) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int c = blockIdx.y;
     if (k >= n) return;
-    v[(int64_t)c * n + k] = s[c] * src[(int64_t)c * n + k];
+    const ff sc = split_d(s[c]);
+    const cff x = ld_c(src + (int64_t)c * n + k);
+    ff r = {0.f, 0.f}, i = {0.f, 0.f};
+    acc_mul(r, sc, x.re);
+    acc_mul(i, sc, x.im);
+    st_c(v + (int64_t)c * n + k, cff{r, i});
 }
 
-void launch_scale_vec(cplx<double>* v, const cplx<double>* src, const double* s, int64_t n,
-                      int nrhs, cudaStream_t st) {
+void launch_scale_vec(float4* v, const float4* src, const double* s, int64_t n, int nrhs, cudaStream_t st) {
     dim3 grid((unsigned)((n + 255) / 256), nrhs);
     scale_vec_kernel<<<grid, 256, 0, st>>>(v, src, s, n);
 }
 
-__global__ void conj_kernel(cplx<double>* v, int64_t count) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < count) v[k].im = -v[k].im;
-}
-
 // ---- fused multi-vector kernels of classical Gram-Schmidt: one pass over w
-// and every V_i (V given as a device array of pointers)
+// and every V_i (V given as a device array of pointers to float-float vectors)
 
-__global__ void mdots_partial_kernel(const cplx<double>* const* __restrict__ V, int nv,
-                                     const cplx<double>* __restrict__ w, int64_t n, int nrhs,
-                                     cplx<double>* partial, int nblk) {
+__global__ void mdots_partial_kernel(const float4* const* __restrict__ V, int nv, const float4* __restrict__ w,
+                                     int64_t n, int nrhs, cplx<double>* partial, int nblk) {
     __shared__ ff sr[8][DOT_NT / 32], si[8][DOT_NT / 32];
     const int blk = blockIdx.x, c = blockIdx.y, i0 = blockIdx.z * 8;
     const int nvb = min(8, nv - i0);
     const int64_t chunk = (n + nblk - 1) / nblk;
     const int64_t k0 = (int64_t)blk * chunk, k1 = min(n, k0 + chunk);
-    const cplx<double>* wc = w + (int64_t)c * n;
+    const float4* wc = w + (int64_t)c * n;
+    const float4* vp[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) vp[i] = (i < nvb ? V[i0 + i] : w) + (int64_t)c * n;
     ff ar[8], ai[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) ar[i] = ai[i] = ff{0.f, 0.f};
     for (int64_t k = k0 + threadIdx.x; k < k1; k += DOT_NT) {
-        const cplx<double> bw = wc[k];
-        const ff br = split_d(bw.re), bi = split_d(bw.im);
+        const cff bw = ld_c(wc + k);
+        cff av[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (i < nvb) av[i] = ld_c(vp[i] + k);
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             if (i < nvb) {
-                const cplx<double> av = V[i0 + i][(int64_t)c * n + k];
-                const ff vr = split_d(av.re), vi = split_d(av.im);
                 // conj(v) w = (vr br + vi bi) + i (vr bi - vi br)
-                acc_mul(ar[i], vr, br);
-                acc_mul(ar[i], vi, bi);
-                acc_mul(ai[i], vr, bi);
-                acc_mul(ai[i], ff_neg(vi), br);
+                acc_mul(ar[i], av[i].re, bw.re);
+                acc_mul(ar[i], av[i].im, bw.im);
+                acc_mul(ai[i], av[i].re, bw.im);
+                acc_mul(ai[i], ff_neg(av[i].im), bw.re);
             }
         }
     }
@@ -310,21 +269,26 @@ __global__ void mdots_partial_kernel(const cplx<double>* const* __restrict__ V, 
     }
 }
 
-// squared norms |v[c]|^2 into out[c] (imaginary part 0), float-float
-__global__ void norms_partial_kernel(const cplx<double>* __restrict__ v, int64_t n,
-                                     cplx<double>* partial, int nblk) {
+// squared norms |v[c]|^2 into out[c] (imaginary part 0), float-float; two
+// entries per thread and step, their loads issued together
+template <typename VV>
+__global__ void norms_partial_kernel(const VV* __restrict__ v, int64_t n, cplx<double>* partial, int nblk) {
     __shared__ ff sr[DOT_NT / 32];
     const int blk = blockIdx.x, c = blockIdx.y;
     const int64_t chunk = (n + nblk - 1) / nblk;
     const int64_t k0 = (int64_t)blk * chunk, k1 = min(n, k0 + chunk);
-    const cplx<double>* vc = v + (int64_t)c * n;
-    ff a = {0.f, 0.f};
-    for (int64_t k = k0 + threadIdx.x; k < k1; k += DOT_NT) {
-        const cplx<double> x = vc[k];
-        const ff xr = split_d(x.re), xi = split_d(x.im);
-        acc_mul(a, xr, xr);
-        acc_mul(a, xi, xi);
+    const VV* vc = v + (int64_t)c * n;
+    ff a = {0.f, 0.f}, a2 = {0.f, 0.f};
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += 2 * DOT_NT) {
+        const bool two = k + DOT_NT < k1;
+        const cff x = ld_c(vc + k);
+        const cff y = two ? ld_c(vc + k + DOT_NT) : cff{{0.f, 0.f}, {0.f, 0.f}};
+        acc_mul(a, x.re, x.re);
+        acc_mul(a, x.im, x.im);
+        acc_mul(a2, y.re, y.re);
+        acc_mul(a2, y.im, y.im);
     }
+    a = ff_sum(a, a2);
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
     for (int o = 16; o > 0; o >>= 1) a = ff_sum(a, shfl_down_ff(a, o));
     if (lane == 0) sr[wp] = a;
@@ -336,27 +300,33 @@ __global__ void norms_partial_kernel(const cplx<double>* __restrict__ v, int64_t
     }
 }
 
-void launch_norms2(const cplx<double>* v, int64_t n, int nrhs, cplx<double>* out,
-                   cplx<double>* partial, int nblk, cudaStream_t st) {
+template <typename VV>
+void launch_norms2(const VV* v, int64_t n, int nrhs, cplx<double>* out, cplx<double>* partial, int nblk,
+                   cudaStream_t st) {
     dim3 grid(nblk, nrhs);
-    norms_partial_kernel<<<grid, DOT_NT, 0, st>>>(v, n, partial, nblk);
+    norms_partial_kernel<VV><<<grid, DOT_NT, 0, st>>>(v, n, partial, nblk);
     dots_final_kernel<<<(nrhs + 127) / 128, 128, 0, st>>>(partial, nblk, nrhs, out);
 }
+template void launch_norms2<cplx<double>>(const cplx<double>*, int64_t, int, cplx<double>*, cplx<double>*, int,
+                                          cudaStream_t);
+template void launch_norms2<float4>(const float4*, int64_t, int, cplx<double>*, cplx<double>*, int,
+                                    cudaStream_t);
 
-void launch_mdots(const cplx<double>* const* V, int nv, const cplx<double>* w, int64_t n, int nrhs,
-                  cplx<double>* out, cplx<double>* partial, int nblk, cudaStream_t st) {
+void launch_mdots(const float4* const* V, int nv, const float4* w, int64_t n, int nrhs, cplx<double>* out,
+                  cplx<double>* partial, int nblk, cudaStream_t st) {
     dim3 grid(nblk, nrhs, (nv + 7) / 8);
     mdots_partial_kernel<<<grid, DOT_NT, 0, st>>>(V, nv, w, n, nrhs, partial, nblk);
     int count = nv * nrhs;
     dots_final_kernel<<<(count + 127) / 128, 128, 0, st>>>(partial, nblk, count, out);
 }
 
-// w[c] += sign * sum_i coef[i*nrhs+c] V_i[c], accumulated in float-float; the
-// block's coefficients (one right-hand side per block row) are split once into
-// shared memory
-__global__ void mcombo_kernel(cplx<double>* w, const cplx<double>* const* __restrict__ V, int nv,
-                              const cplx<double>* __restrict__ coef, int64_t n, int nrhs,
-                              double sign) {
+// w[c] += sign * sum_i coef[i*nrhs+c] V_i[c], accumulated in float-float; w is
+// a float-float work vector (Gram-Schmidt) or the complex128 solution (its
+// update); the block's coefficients (one right-hand side per block row) are
+// split once into shared memory
+template <typename VW>
+__global__ void mcombo_kernel(VW* w, const float4* const* __restrict__ V, int nv,
+                              const cplx<double>* __restrict__ coef, int64_t n, int nrhs, double sign) {
     __shared__ ff scr[64], sci[64];
     const int c = blockIdx.y;
     const float sg = sign < 0 ? -1.f : 1.f;  // sign is +-1
@@ -369,25 +339,34 @@ __global__ void mcombo_kernel(cplx<double>* w, const cplx<double>* const* __rest
     __syncthreads();
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const cplx<double> w0 = w[(int64_t)c * n + k];
-    ff ar = split_d(w0.re), ai = split_d(w0.im);
+    const cff w0 = ld_c(w + (int64_t)c * n + k);
+    ff ar = w0.re, ai = w0.im;
     for (int i = 0; i < nv; ++i) {
         const ff cr = scr[i], ci = sci[i];
-        const cplx<double> v = V[i][(int64_t)c * n + k];
-        const ff vr = split_d(v.re), vi = split_d(v.im);
+        const cff v = ld_c(V[i] + (int64_t)c * n + k);
         // (cr + i ci)(vr + i vi)
-        acc_mul(ar, cr, vr);
-        acc_mul(ar, ff_neg(ci), vi);
-        acc_mul(ai, cr, vi);
-        acc_mul(ai, ci, vr);
+        acc_mul(ar, cr, v.re);
+        acc_mul(ar, ff_neg(ci), v.im);
+        acc_mul(ai, cr, v.im);
+        acc_mul(ai, ci, v.re);
     }
-    w[(int64_t)c * n + k] = mk<double>(join_d(ar), join_d(ai));
+    st_c(w + (int64_t)c * n + k, cff{ar, ai});
 }
 
-void launch_mcombo(cplx<double>* w, const cplx<double>* const* V, int nv, const cplx<double>* coef,
-                   int64_t n, int nrhs, double sign, cudaStream_t st) {
+template <typename VW>
+void launch_mcombo(VW* w, const float4* const* V, int nv, const cplx<double>* coef, int64_t n, int nrhs,
+                   double sign, cudaStream_t st) {
     dim3 grid((unsigned)((n + 255) / 256), nrhs);
-    mcombo_kernel<<<grid, 256, 0, st>>>(w, V, nv, coef, n, nrhs, sign);
+    mcombo_kernel<VW><<<grid, 256, 0, st>>>(w, V, nv, coef, n, nrhs, sign);
+}
+template void launch_mcombo<float4>(float4*, const float4* const*, int, const cplx<double>*, int64_t, int, double,
+                                    cudaStream_t);
+template void launch_mcombo<cplx<double>>(cplx<double>*, const float4* const*, int, const cplx<double>*, int64_t,
+                                          int, double, cudaStream_t);
+
+__global__ void conj_kernel(cplx<double>* v, int64_t count) {
+    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < count) v[k].im = -v[k].im;
 }
 
 void launch_conj(cplx<double>* v, int64_t count, cudaStream_t st) {

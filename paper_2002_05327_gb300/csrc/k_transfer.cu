@@ -14,6 +14,8 @@
 //
 // assemble: u_DDM = sum_l sum_ij beta_{0,0;ij} u^l_ij (Eq. 3.x / 4.x), summed
 // per global node over the at most 2^n boxes whose cutoff reaches it.
+#include <type_traits>
+
 #include "helm_internal.h"
 #include "ff.h"
 
@@ -31,12 +33,21 @@ __device__ __forceinline__ T beta1(int dir, int k, int blo, int bhi, int d, cons
 constexpr int kMaxIncoming = 32;  // routing gives at most 8 (2D) / 26 (3D); the host checks
 constexpr int kRG = 8;             // right-hand sides per thread
 
+// an entry of the global source (complex128, or float-float for the Krylov
+// work vectors) in the window precision, off the FP64 pipe for complex64
 template <typename T>
 __device__ __forceinline__ cplx<T> src_cast(cplx<double> v) {
     if constexpr (sizeof(T) == 4)
-        return mk<float>(ffa::d2f(v.re), ffa::d2f(v.im));  // off the FP64 pipe
+        return mk<float>(ffa::d2f(v.re), ffa::d2f(v.im));
     else
         return v;
+}
+template <typename T>
+__device__ __forceinline__ cplx<T> src_cast(float4 v) {
+    if constexpr (sizeof(T) == 4)
+        return mk<float>(v.x + v.y, v.z + v.w);
+    else
+        return mk<double>(ffa::join_d({v.x, v.y}), ffa::join_d({v.z, v.w}));
 }
 
 // Block = up to kGB consecutive nodes of one task's work list (GNode: the
@@ -45,7 +56,7 @@ __device__ __forceinline__ cplx<T> src_cast(cplx<double> v) {
 // The task's incoming transfers are staged in shared memory; each thread
 // handles kRG right-hand sides with independent loads and sums the transfers
 // in the order of the incoming list.
-template <typename T>
+template <typename T, typename VB>
 __global__ void __launch_bounds__(kGB) gather_kernel(const GBlock* __restrict__ blocks,
                                                      const GNode* __restrict__ nodes,
                                                      const Task* __restrict__ tasks,
@@ -55,7 +66,7 @@ __global__ void __launch_bounds__(kGB) gather_kernel(const GBlock* __restrict__ 
                                                      const cplx<T>* __restrict__ an,
                                                      const cplx<T>* __restrict__ af,
                                                      const T* __restrict__ tab,
-                                                     const cplx<double>* __restrict__ b, int nrhs,
+                                                     const VB* __restrict__ b, int nrhs,
                                                      const cplx<T>* __restrict__ buf, cplx<T>* bsrc,
                                                      int64_t rstride) {
     struct InS {
@@ -162,14 +173,14 @@ __global__ void __launch_bounds__(kGB) gather_kernel(const GBlock* __restrict__ 
         if (c < nc) out[(int64_t)c * rstride] = val[c];
 }
 
-template <typename T>
+template <typename T, typename VB>
 void launch_gather(const GBlock* blocks, int nblocks, const GNode* nodes, const Task* tasks,
                    const SubDesc* subs, const Incoming* inc, const DevProblem& P, const T* m,
-                   const cplx<T>* an, const cplx<T>* af, const T* beta_tab, const cplx<double>* b, int nrhs,
+                   const cplx<T>* an, const cplx<T>* af, const T* beta_tab, const VB* b, int nrhs,
                    const cplx<T>* buf, cplx<T>* bsrc, int64_t rstride, cudaStream_t st) {
     if (nblocks == 0) return;
     dim3 grid((unsigned)nblocks, (nrhs + kRG - 1) / kRG);
-    gather_kernel<T><<<grid, kGB, 0, st>>>(blocks, nodes, tasks, subs, inc, P, T(1.0 / (P.h * P.h)),
+    gather_kernel<T, VB><<<grid, kGB, 0, st>>>(blocks, nodes, tasks, subs, inc, P, T(1.0 / (P.h * P.h)),
                                            T(P.omega * P.omega), m, an, af, beta_tab, b, nrhs, buf, bsrc,
                                            rstride);
 }
@@ -177,12 +188,11 @@ void launch_gather(const GBlock* blocks, int nblocks, const GNode* nodes, const 
 // ----------------------------------------------------------------------------- assembly
 constexpr int kAG = 8;  // right-hand sides per assembly thread
 
-template <typename T>
+template <typename T, typename VU>
 __global__ void assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs,
                                 const int* __restrict__ box_of, const int64_t* __restrict__ node_buf,
                                 int nsweeps, const T* __restrict__ tab,
-                                const cplx<T>* __restrict__ buf, int64_t rstride, int nrhs,
-                                cplx<double>* U) {
+                                const cplx<T>* __restrict__ buf, int64_t rstride, int nrhs, VU* U) {
     // one thread per (global node, group of kAG right-hand sides): the boxes
     // whose cutoff reaches the node and their weights are found once, then
     // applied to the group with independent loads
@@ -300,38 +310,40 @@ __global__ void assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs,
 #pragma unroll
     for (int c = 0; c < kAG; ++c) {
         if (c0 + c >= nrhs) continue;
-        if constexpr (kF32)
-            U[(int64_t)(c0 + c) * Ng + k] = mk<double>(ffa::join_d(fr[c]), ffa::join_d(fi[c]));
-        else
+        if constexpr (!kF32 && std::is_same<VU, cplx<double>>::value) {
             U[(int64_t)(c0 + c) * Ng + k] = mk<double>(sr[c], si[c]);
+        } else {
+            if constexpr (!kF32) {
+                fr[c] = ffa::split_d(sr[c]);
+                fi[c] = ffa::split_d(si[c]);
+            }
+            ffa::st_c(U + (int64_t)(c0 + c) * Ng + k, ffa::cff{fr[c], fi[c]});
+        }
     }
 }
 
-template <typename T>
+template <typename T, typename VU>
 void launch_assemble(const DevProblem& P, const SubDesc* subs, const int* box_of,
                      const int64_t* node_buf, int nsweeps, const T* beta_tab,
-                     const cplx<T>* buf, int64_t rstride, int nrhs, cplx<double>* U,
-                     cudaStream_t st) {
+                     const cplx<T>* buf, int64_t rstride, int nrhs, VU* U, cudaStream_t st) {
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
     const int nt = 256;
     dim3 grid((unsigned)((Ng + nt - 1) / nt), (nrhs + kAG - 1) / kAG);
-    assemble_kernel<T><<<grid, nt, 0, st>>>(P, subs, box_of, node_buf, nsweeps, beta_tab, buf, rstride, nrhs,
+    assemble_kernel<T, VU><<<grid, nt, 0, st>>>(P, subs, box_of, node_buf, nsweeps, beta_tab, buf, rstride, nrhs,
                                             U);
 }
 
-template void launch_gather<float>(const GBlock*, int, const GNode*, const Task*, const SubDesc*,
-                                   const Incoming*, const DevProblem&, const float*, const cplx<float>*,
-                                   const cplx<float>*, const float*, const cplx<double>*, int,
-                                   const cplx<float>*, cplx<float>*, int64_t, cudaStream_t);
-template void launch_gather<double>(const GBlock*, int, const GNode*, const Task*, const SubDesc*,
-                                    const Incoming*, const DevProblem&, const double*, const cplx<double>*,
-                                    const cplx<double>*, const double*, const cplx<double>*, int,
-                                    const cplx<double>*, cplx<double>*, int64_t, cudaStream_t);
-template void launch_assemble<float>(const DevProblem&, const SubDesc*, const int*,
-                                     const int64_t*, int, const float*, const cplx<float>*,
-                                     int64_t, int, cplx<double>*, cudaStream_t);
-template void launch_assemble<double>(const DevProblem&, const SubDesc*, const int*,
-                                      const int64_t*, int, const double*, const cplx<double>*,
-                                      int64_t, int, cplx<double>*, cudaStream_t);
+#define HELM_TRANSFER_INST(T, V)                                                                          \
+    template void launch_gather<T, V>(const GBlock*, int, const GNode*, const Task*, const SubDesc*,           \
+                                      const Incoming*, const DevProblem&, const T*, const cplx<T>*,            \
+                                      const cplx<T>*, const T*, const V*, int, const cplx<T>*, cplx<T>*,       \
+                                      int64_t, cudaStream_t);                                                  \
+    template void launch_assemble<T, V>(const DevProblem&, const SubDesc*, const int*, const int64_t*, int,    \
+                                        const T*, const cplx<T>*, int64_t, int, V*, cudaStream_t);
+HELM_TRANSFER_INST(float, cplx<double>)
+HELM_TRANSFER_INST(float, float4)
+HELM_TRANSFER_INST(double, cplx<double>)
+HELM_TRANSFER_INST(double, float4)
+#undef HELM_TRANSFER_INST
 
 }  // namespace helm

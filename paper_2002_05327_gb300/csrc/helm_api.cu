@@ -172,7 +172,6 @@ struct helm_ctx {
     float4** zptr_d = nullptr;
     cplx<double>* small_d = nullptr;  // dots / coefficients
     cplx<double>* partial_d = nullptr;
-    double* scal_d = nullptr;
     size_t small_cap = 0;
     size_t dev_bytes = 0;
 
@@ -271,10 +270,8 @@ int ensure_small(helm_ctx* c, size_t count) {
     if (count <= c->small_cap) return HELM_OK;
     if (c->small_d) cudaFree(c->small_d);
     if (c->partial_d) cudaFree(c->partial_d);
-    if (c->scal_d) cudaFree(c->scal_d);
     CK(cudaMalloc(&c->small_d, count * sizeof(cplx<double>)));
-    CK(cudaMalloc(&c->partial_d, count * 1024 * sizeof(cplx<double>)));
-    CK(cudaMalloc(&c->scal_d, count * sizeof(double)));
+    CK(cudaMalloc(&c->partial_d, count * 256 * sizeof(cplx<double>)));  // <= 256 block partials per output
     if (!c->vptr_d) {
         CK(cudaMalloc(&c->vptr_d, 64 * sizeof(void*)));
         CK(cudaMalloc(&c->zptr_d, 64 * sizeof(void*)));
@@ -921,7 +918,7 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
     // vectors, allocated as the Krylov space grows: scratch w (0), then
     // V_i at 1 + 2i and Z_i at 2 + 2i
     TRY(ensure_gm(c, nrhs, 2));
-    TRY(ensure_small(c, (size_t)(m + 2) * nrhs));
+    TRY(ensure_small(c, (size_t)2 * (m + 2) * nrhs));  // coefficients, then the fused kernels' dots
     const int nblk = (int)std::min<int64_t>(256, (Ng + 4095) / 4096);
     // work vectors in float-float form (one float4 per complex entry)
     auto fv = [&](int i) { return reinterpret_cast<float4*>(c->gm[i]); };
@@ -930,7 +927,6 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
     auto Z = [&](int i) { return fv(2 + 2 * i); };
     std::vector<double> bn(nrhs), res(nrhs, 1.0);
     std::vector<cplx<double>> hd((size_t)(m + 2) * nrhs);
-    std::vector<double> sc(nrhs);
     auto norms = [&](const auto* v, std::vector<double>& out) -> int {
         { ProfScope ps_(c, HELM_K_KRYLOV, 2); launch_norms2(v, Ng, nrhs, c->small_d, c->partial_d, nblk, c->stream); }
         CK(cudaMemcpyAsync(hd.data(), c->small_d, nrhs * 16, cudaMemcpyDeviceToHost, c->stream));
@@ -960,9 +956,15 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
             break;
         }
         if (total >= maxit) break;
-        for (int r = 0; r < nrhs; ++r) sc[r] = beta[r] > 0 ? 1.0 / beta[r] : 0.0;
-        CK(cudaMemcpyAsync(c->scal_d, sc.data(), nrhs * 8, cudaMemcpyHostToDevice, c->stream));
-        { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_scale_vec(V(0), w, c->scal_d, Ng, nrhs, c->stream); }
+        // The basis is kept unnormalised: u_i = s_i v_i with the scale s_i of
+        // every right-hand side held here, folded into the Gram-Schmidt
+        // coefficients (u_i^H w = s_i v_i^H w; w - sum (v_i^H w) v_i =
+        // w - sum (u_i^H w / s_i^2) u_i) and the final combination
+        // (z'_k = M^-1 u_k = s_k z_k).  u_0 = r_0 is w itself: the buffers swap.
+        std::swap(c->gm[0], c->gm[1]);
+        w = fv(0);
+        std::vector<std::vector<double>> sv(m + 1, std::vector<double>(nrhs, 1.0));
+        for (int r = 0; r < nrhs; ++r) sv[0][r] = beta[r] > 0 ? beta[r] : 1.0;
         // per-RHS Hessenberg (column-major, (m+1) x m), Givens, residual vector g
         std::vector<std::vector<cd>> H(nrhs, std::vector<cd>((size_t)(m + 1) * m, 0.0));
         std::vector<std::vector<double>> cs(nrhs, std::vector<double>(m, 0));
@@ -980,8 +982,13 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
             w = fv(0);
             TRY(apply_ddm_dev(c, nrhs, V(k), Z(k)));
             ++apps;
-            // w = -A z_k (apply_A with no b); CGS2 on w: h = V^H w, w -= V h, twice.
-            // Then A z_k = sum_i (-h_i) v_i + |w| v_{k+1} with v_{k+1} = -w/|w|.
+            // w = -A z'_k (apply_A with no b); CGS2 on w against the u_i: the
+            // dots d = U^H w, then w -= sum (d_i / s_i^2) u_i, twice.  The
+            // first combination also forms the second pass's dots, the second
+            // the norm of what is left (fused kernels when k + 1 <= 8).  With
+            // h_i = sum over the passes of d_i / s_i (= v_i^H w):
+            //   A z_k = sum_i (-h_i / s_k) v_i - (|w| / s_k) v_{k+1},
+            // v_{k+1} = w / |w|, stored unnormalised as u_{k+1} = w, s_{k+1} = |w|.
             {
                 ProfScope ps_(c, HELM_K_KRYLOV, 1);
                 launch_apply_A(c->P, c->stc_d, nullptr, Z(k), w, nrhs, c->stream);
@@ -993,30 +1000,71 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
                 CK(cudaMemcpyAsync(c->vptr_d, vp.data(), vp.size() * sizeof(void*),
                                    cudaMemcpyHostToDevice, c->stream));
             }
-            for (int pass = 0; pass < 2; ++pass) {
-                { ProfScope ps_(c, HELM_K_KRYLOV, 2); launch_mdots(c->vptr_d, k + 1, w, Ng, nrhs, c->small_d, c->partial_d, nblk, c->stream); }
-                CK(cudaMemcpyAsync(hd.data(), c->small_d, (size_t)(k + 1) * nrhs * 16,
-                                   cudaMemcpyDeviceToHost, c->stream));
-                CK(cudaStreamSynchronize(c->stream));
+            const bool fused = k + 1 <= kComboDotsMax;
+            std::vector<cplx<double>> coef((size_t)(k + 1) * nrhs);
+            // dots d (in hd) -> h sums and the combination coefficients -d_i / s_i^2
+            auto take_dots = [&]() {
                 for (int i = 0; i <= k; ++i)
-                    for (int r = 0; r < nrhs; ++r)
-                        hsum[r][i] += cd(hd[(size_t)i * nrhs + r].re, hd[(size_t)i * nrhs + r].im);
-                { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_mcombo(w, c->vptr_d, k + 1, c->small_d, Ng, nrhs, -1.0, c->stream); }
-            }
+                    for (int r = 0; r < nrhs; ++r) {
+                        const cd d(hd[(size_t)i * nrhs + r].re, hd[(size_t)i * nrhs + r].im);
+                        hsum[r][i] += d / sv[i][r];
+                        const cd cf = -d / (sv[i][r] * sv[i][r]);
+                        coef[(size_t)i * nrhs + r] = {cf.real(), cf.imag()};
+                    }
+                return cudaMemcpyAsync(c->small_d, coef.data(), coef.size() * 16, cudaMemcpyHostToDevice,
+                                       c->stream);
+            };
+            auto fetch = [&](size_t count) -> int {
+                CK(cudaMemcpyAsync(hd.data(), c->small_d, count * 16, cudaMemcpyDeviceToHost, c->stream));
+                CK(cudaStreamSynchronize(c->stream));
+                return HELM_OK;
+            };
+            { ProfScope ps_(c, HELM_K_KRYLOV, 2); launch_mdots(c->vptr_d, k + 1, w, Ng, nrhs, c->small_d, c->partial_d, nblk, c->stream); }
+            TRY(fetch((size_t)(k + 1) * nrhs));
+            CK(take_dots());
             std::vector<double> wn(nrhs);
-            TRY(norms(w, wn));
+            if (fused) {
+                {
+                    ProfScope ps_(c, HELM_K_KRYLOV, 2);
+                    launch_combo_dots(w, c->vptr_d, k + 1, c->small_d, Ng, nrhs, true, c->small_d + coef.size(),
+                                      c->partial_d, nblk, c->stream);
+                }
+                CK(cudaMemcpyAsync(hd.data(), c->small_d + coef.size(), coef.size() * 16, cudaMemcpyDeviceToHost,
+                                   c->stream));
+                CK(cudaStreamSynchronize(c->stream));
+                CK(take_dots());
+                {
+                    ProfScope ps_(c, HELM_K_KRYLOV, 2);
+                    launch_combo_dots(w, c->vptr_d, k + 1, c->small_d, Ng, nrhs, false, c->small_d + coef.size(),
+                                      c->partial_d, nblk, c->stream);
+                }
+                CK(cudaMemcpyAsync(hd.data(), c->small_d + coef.size(), nrhs * 16, cudaMemcpyDeviceToHost,
+                                   c->stream));
+                CK(cudaStreamSynchronize(c->stream));
+                for (int r = 0; r < nrhs; ++r) wn[r] = std::sqrt(std::max(0.0, hd[r].re));
+            } else {
+                { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_mcombo(w, c->vptr_d, k + 1, c->small_d, Ng, nrhs, 1.0, c->stream); }
+                { ProfScope ps_(c, HELM_K_KRYLOV, 2); launch_mdots(c->vptr_d, k + 1, w, Ng, nrhs, c->small_d + coef.size(), c->partial_d, nblk, c->stream); }
+                CK(cudaMemcpyAsync(hd.data(), c->small_d + coef.size(), coef.size() * 16, cudaMemcpyDeviceToHost,
+                                   c->stream));
+                CK(cudaStreamSynchronize(c->stream));
+                CK(take_dots());
+                { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_mcombo(w, c->vptr_d, k + 1, c->small_d, Ng, nrhs, 1.0, c->stream); }
+                TRY(norms(w, wn));
+            }
             TRY(check_device_error(c));  // a timed-out preconditioner ends the solve here
-            for (int r = 0; r < nrhs; ++r) sc[r] = wn[r] > 1e-300 ? -1.0 / wn[r] : 0.0;
-            CK(cudaMemcpyAsync(c->scal_d, sc.data(), nrhs * 8, cudaMemcpyHostToDevice, c->stream));
-            { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_scale_vec(V(k + 1), w, c->scal_d, Ng, nrhs, c->stream); }
+            // u_{k+1} = w: the buffers swap
+            std::swap(c->gm[0], c->gm[1 + 2 * (k + 1)]);
+            w = fv(0);
+            for (int r = 0; r < nrhs; ++r) sv[k + 1][r] = wn[r] > 1e-300 ? wn[r] : 1.0;
             ++total;
             bool all = true;
             maxres = 0;
             for (int r = 0; r < nrhs; ++r) {
                 if (done[r]) continue;
                 std::vector<cd>& Hr = H[r];
-                for (int i = 0; i <= k; ++i) Hr[(size_t)k * (m + 1) + i] = -hsum[r][i];
-                Hr[(size_t)k * (m + 1) + k + 1] = wn[r];
+                for (int i = 0; i <= k; ++i) Hr[(size_t)k * (m + 1) + i] = -hsum[r][i] / sv[k][r];
+                Hr[(size_t)k * (m + 1) + k + 1] = -wn[r] / sv[k][r];
                 for (int i = 0; i < k; ++i) {
                     cd a = Hr[(size_t)k * (m + 1) + i], bb = Hr[(size_t)k * (m + 1) + i + 1];
                     Hr[(size_t)k * (m + 1) + i] = cs[r][i] * a + sn[r][i] * bb;
@@ -1059,7 +1107,8 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
                 for (int j2 = i + 1; j2 < kk; ++j2) s -= H[r][(size_t)j2 * (m + 1) + i] * y[j2];
                 y[i] = s / H[r][(size_t)i * (m + 1) + i];
             }
-            for (int i = 0; i < kk; ++i) coef[(size_t)i * nrhs + r] = {y[i].real(), y[i].imag()};
+            // x += sum y_i z_i = sum (y_i / s_i) z'_i
+            for (int i = 0; i < kk; ++i) coef[(size_t)i * nrhs + r] = {y[i].real() / sv[i][r], y[i].imag() / sv[i][r]};
         }
         CK(cudaMemcpyAsync(c->small_d, coef.data(), coef.size() * 16, cudaMemcpyHostToDevice,
                            c->stream));
@@ -1433,7 +1482,7 @@ void helm_destroy(helm_ctx* c) {
                     c->Pv64, c->inva64, c->Pv32, c->inva32, c->tab64, c->tab32, c->box_of,
                     c->fac, c->err_d, c->tasks_d, c->inc_d, c->gnode_d, c->gblk_d, c->node_buf_d, c->buf,
                     c->bvec,
-                    c->small_d, c->partial_d, c->scal_d, c->vptr_d, c->zptr_d, c->ascale_d, c->bsrc,
+                    c->small_d, c->partial_d, c->vptr_d, c->zptr_d, c->ascale_d, c->bsrc,
                     c->stc_d};
     for (void* p : ptrs)
         if (p) cudaFree(p);

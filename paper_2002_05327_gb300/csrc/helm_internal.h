@@ -265,8 +265,12 @@ void launch_mdots(const float4* const* V, int nv, const float4* w, int64_t n, in
 template <typename VW>
 void launch_mcombo(VW* w, const float4* const* V, int nv, const cplx<double>* coef, int64_t n, int nrhs,
                    double sign, cudaStream_t st);  // w[c] += sign * sum_i coef[i*nrhs+c] V_i[c]
-void launch_scale_vec(float4* v, const float4* src, const double* s, int64_t n, int nrhs,
-                      cudaStream_t st);  // v[c] = src[c] * s[c]
+// w[c] += sum_i coef[i*nrhs+c] U_i[c] fused with, of the updated w, the dots
+// out[i*nrhs+c] = <U_i[c], w[c]> (want_dots) or the squared norms out[c]; nv <= 8
+constexpr int kComboDotsMax = 8;
+void launch_combo_dots(float4* w, const float4* const* U, int nv, const cplx<double>* coef, int64_t n, int nrhs,
+                       bool want_dots, cplx<double>* out, cplx<double>* partial, int nblk, cudaStream_t st);
+  // v[c] = src[c] * s[c]
 void launch_conj(cplx<double>* v, int64_t count, cudaStream_t st);
 void launch_gradient(const DevProblem& P, const Win<double>& g, const cplx<double>* U,
                      const cplx<double>* L, int nsrc, double* grad, cudaStream_t st);

@@ -192,39 +192,21 @@ __global__ void dots_final_kernel(const cplx<double>* partial, int nblk, int cou
     out[t] = mk<double>(r, i);
 }
 
-// v = s * src for a per-right-hand-side real scale s (float-float vectors)
-__global__ void scale_vec_kernel(float4* v, const float4* __restrict__ src, const double* __restrict__ s,
-                                 int64_t n) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = blockIdx.y;
-    if (k >= n) return;
-    const ff sc = split_d(s[c]);
-    const cff x = ld_c(src + (int64_t)c * n + k);
-    ff r = {0.f, 0.f}, i = {0.f, 0.f};
-    acc_mul(r, sc, x.re);
-    acc_mul(i, sc, x.im);
-    st_c(v + (int64_t)c * n + k, cff{r, i});
-}
-
-void launch_scale_vec(float4* v, const float4* src, const double* s, int64_t n, int nrhs, cudaStream_t st) {
-    dim3 grid((unsigned)((n + 255) / 256), nrhs);
-    scale_vec_kernel<<<grid, 256, 0, st>>>(v, src, s, n);
-}
-
 // ---- fused multi-vector kernels of classical Gram-Schmidt: one pass over w
 // and every V_i (V given as a device array of pointers to float-float vectors)
 
-__global__ void mdots_partial_kernel(const float4* const* __restrict__ V, int nv, const float4* __restrict__ w,
-                                     int64_t n, int nrhs, cplx<double>* partial, int nblk) {
+__global__ void __launch_bounds__(DOT_NT, 2) mdots_partial_kernel(const float4* const* __restrict__ V, int nv,
+                                                                   const float4* __restrict__ w, int64_t n,
+                                                                   int nrhs, cplx<double>* partial, int nblk) {
     __shared__ ff sr[8][DOT_NT / 32], si[8][DOT_NT / 32];
+    __shared__ const float4* svp[8];
     const int blk = blockIdx.x, c = blockIdx.y, i0 = blockIdx.z * 8;
     const int nvb = min(8, nv - i0);
     const int64_t chunk = (n + nblk - 1) / nblk;
     const int64_t k0 = (int64_t)blk * chunk, k1 = min(n, k0 + chunk);
     const float4* wc = w + (int64_t)c * n;
-    const float4* vp[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) vp[i] = (i < nvb ? V[i0 + i] : w) + (int64_t)c * n;
+    if ((int)threadIdx.x < nvb) svp[threadIdx.x] = V[i0 + threadIdx.x] + (int64_t)c * n;
+    __syncthreads();
     ff ar[8], ai[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) ar[i] = ai[i] = ff{0.f, 0.f};
@@ -233,7 +215,7 @@ __global__ void mdots_partial_kernel(const float4* const* __restrict__ V, int nv
         cff av[8];
 #pragma unroll
         for (int i = 0; i < 8; ++i)
-            if (i < nvb) av[i] = ld_c(vp[i] + k);
+            if (i < nvb) av[i] = ld_c(svp[i] + k);  // vector pointers from shared memory
 #pragma unroll
         for (int i = 0; i < 8; ++i) {
             if (i < nvb) {
@@ -363,6 +345,101 @@ template void launch_mcombo<float4>(float4*, const float4* const*, int, const cp
                                     cudaStream_t);
 template void launch_mcombo<cplx<double>>(cplx<double>*, const float4* const*, int, const cplx<double>*, int64_t,
                                           int, double, cudaStream_t);
+
+// w[c] += sum_i coef[i*nrhs+c] U_i[c] in float-float, fused with the reduction
+// the next Gram-Schmidt step needs of the updated w: its dots <U_i[c], w[c]>
+// with every U_i (want_dots) or its squared norm (into slot 0).  One pass over
+// w and the U_i (nv <= 8, one right-hand side per block row, a fixed chunk
+// per block as in the dot kernels); the dots are taken of w as stored.
+__global__ void __launch_bounds__(DOT_NT, 2) combo_dots_kernel(float4* w, const float4* const* __restrict__ U, int nv,
+                                  const cplx<double>* __restrict__ coef, int64_t n, int nrhs, int want_dots,
+                                  cplx<double>* partial, int nblk) {
+    __shared__ ff scr[8], sci[8];
+    __shared__ const float4* sup[8];
+    __shared__ ff sr[8][DOT_NT / 32], si[8][DOT_NT / 32];
+    const int blk = blockIdx.x, c = blockIdx.y;
+    if ((int)threadIdx.x < nv) {
+        const cplx<double> a = coef[threadIdx.x * nrhs + c];
+        scr[threadIdx.x] = split_d(a.re);
+        sci[threadIdx.x] = split_d(a.im);
+        sup[threadIdx.x] = U[threadIdx.x] + (int64_t)c * n;
+    }
+    __syncthreads();
+    const int64_t chunk = (n + nblk - 1) / nblk;
+    const int64_t k0 = (int64_t)blk * chunk, k1 = min(n, k0 + chunk);
+    float4* wc = w + (int64_t)c * n;
+    ff dr[8], di[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) dr[i] = di[i] = ff{0.f, 0.f};
+    for (int64_t k = k0 + threadIdx.x; k < k1; k += DOT_NT) {
+        const cff w0 = ld_c(wc + k);
+        cff uv[8];
+#pragma unroll
+        for (int i = 0; i < 8; ++i)
+            if (i < nv) uv[i] = ld_c(sup[i] + k);  // vector pointers from shared memory
+        ff ar = w0.re, ai = w0.im;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            if (i < nv) {
+                // (cr + i ci)(ur + i ui), the coefficients read from shared memory
+                const ff cr = scr[i], ci = sci[i];
+                acc_mul(ar, cr, uv[i].re);
+                acc_mul(ar, ff_neg(ci), uv[i].im);
+                acc_mul(ai, cr, uv[i].im);
+                acc_mul(ai, ci, uv[i].re);
+            }
+        }
+        const cff wn = {ff_norm(ar), ff_norm(ai)};
+        wc[k] = make_float4(wn.re.hi, wn.re.lo, wn.im.hi, wn.im.lo);
+        if (want_dots) {
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+                if (i < nv) {
+                    // conj(u) w = (ur wr + ui wi) + i (ur wi - ui wr)
+                    acc_mul(dr[i], uv[i].re, wn.re);
+                    acc_mul(dr[i], uv[i].im, wn.im);
+                    acc_mul(di[i], uv[i].re, wn.im);
+                    acc_mul(di[i], ff_neg(uv[i].im), wn.re);
+                }
+            }
+        } else {
+            acc_mul(dr[0], wn.re, wn.re);
+            acc_mul(dr[0], wn.im, wn.im);
+        }
+    }
+    const int nout = want_dots ? nv : 1;
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+        if (i >= nout) break;
+        for (int o = 16; o > 0; o >>= 1) {
+            dr[i] = ff_sum(dr[i], shfl_down_ff(dr[i], o));
+            di[i] = ff_sum(di[i], shfl_down_ff(di[i], o));
+        }
+        if (lane == 0) {
+            sr[i][wp] = dr[i];
+            si[i][wp] = di[i];
+        }
+    }
+    __syncthreads();
+    if ((int)threadIdx.x < nout) {
+        const int i = threadIdx.x;
+        ff r = {0.f, 0.f}, im = {0.f, 0.f};
+        for (int q = 0; q < DOT_NT / 32; ++q) {
+            r = ff_sum(r, sr[i][q]);
+            im = ff_sum(im, si[i][q]);
+        }
+        partial[((int64_t)i * nrhs + c) * nblk + blk] = mk<double>(join_d(r), join_d(im));
+    }
+}
+
+void launch_combo_dots(float4* w, const float4* const* U, int nv, const cplx<double>* coef, int64_t n, int nrhs,
+                       bool want_dots, cplx<double>* out, cplx<double>* partial, int nblk, cudaStream_t st) {
+    dim3 grid(nblk, nrhs);
+    combo_dots_kernel<<<grid, DOT_NT, 0, st>>>(w, U, nv, coef, n, nrhs, want_dots ? 1 : 0, partial, nblk);
+    const int count = (want_dots ? nv : 1) * nrhs;
+    dots_final_kernel<<<(count + 127) / 128, 128, 0, st>>>(partial, nblk, count, out);
+}
 
 __global__ void conj_kernel(cplx<double>* v, int64_t count) {
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

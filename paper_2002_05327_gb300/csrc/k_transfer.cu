@@ -140,7 +140,10 @@ __global__ void __launch_bounds__(kGB) gather_kernel(const GBlock* __restrict__ 
         while (todo) {  // incoming transfers reaching this node, in list order
             const InS& R = sin[__ffs(todo) - 1];
             todo &= todo - 1;
-            for (int pt = 0; pt < npt; ++pt) {
+            // stencil points (static indices after unrolling: the arrays stay in registers)
+#pragma unroll
+            for (int pt = 0; pt < 7; ++pt) {
+                if (pt >= npt) break;
                 int gg[3] = {g[0], g[1], g[2]};
                 bool ok = true;
                 if (pt > 0) {
@@ -151,7 +154,9 @@ __global__ void __launch_bounds__(kGB) gather_kernel(const GBlock* __restrict__ 
                 }
                 T beta = T(1);
                 int64_t li = 0;
-                for (int a = ndim - 1; a >= 0 && ok; --a) {
+#pragma unroll
+                for (int a = 2; a >= 0; --a) {
+                    if (a >= ndim || !ok) continue;
                     const int xl = gg[a] - R.lo[a];
                     if (xl < 0 || xl >= R.nw[a]) ok = false;  // zero outside the sender window
                     li = li * R.nw[a] + xl;
@@ -205,16 +210,17 @@ __global__ void assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs,
     g[0] = (int)(k % P.N[0]);
     g[1] = (int)((k / P.N[0]) % P.N[1]);
     g[2] = (int)(k / ((int64_t)P.N[0] * P.N[1]));
-    // candidate boxes per axis: own box (cutoff 1) and the neighbour whose
-    // cutoff reaches this node
-    int cb[3][2];
-    T cw[3][2];
-    int cn[3];
+    // candidate boxes per axis in fixed slots: 0 the own box (cutoff 1), 1 the
+    // box above and 2 the box below, each with the weight of its cutoff at this
+    // node (0 where its cutoff does not reach)
+    int cb[3][3];
+    T cw[3][3];
     int off = 0;
+#pragma unroll
     for (int a = 0; a < 3; ++a) {
-        cn[a] = 1;
-        cb[a][0] = 0;
+        cb[a][0] = cb[a][1] = cb[a][2] = 0;
         cw[a][0] = T(1);
+        cw[a][1] = cw[a][2] = T(0);
         if (a >= ndim) continue;
         const int i0 = box_of[off + g[a]];
         off += P.N[a];
@@ -226,18 +232,16 @@ __global__ void assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs,
             const int lo1 = subs[(i0 + 1) * stride].box_lo[a];
             const int mm = lo1 - 1 - g[a];
             if (mm < P.d) {
-                cb[a][cn[a]] = i0 + 1;
-                cw[a][cn[a]] = tab[mm];
-                ++cn[a];
+                cb[a][1] = i0 + 1;
+                cw[a][1] = tab[mm];
             }
         }
         if (i0 > 0) {
             const int hi0 = subs[(i0 - 1) * stride].box_hi[a];
             const int mm = g[a] - hi0;
             if (mm < P.d) {
-                cb[a][cn[a]] = i0 - 1;
-                cw[a][cn[a]] = tab[mm];
-                ++cn[a];
+                cb[a][2] = i0 - 1;
+                cw[a][2] = tab[mm];
             }
         }
     }
@@ -254,18 +258,19 @@ __global__ void assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs,
         wb[ib] = T(0);
     }
 #pragma unroll
-    for (int i0 = 0; i0 < 2; ++i0)
+    for (int i0 = 0; i0 < 3; ++i0)
 #pragma unroll
-        for (int i1 = 0; i1 < 2; ++i1)
+        for (int i1 = 0; i1 < 3; ++i1)
 #pragma unroll
-            for (int i2 = 0; i2 < 2; ++i2) {
-                if (i0 >= cn[0] || i1 >= cn[1] || i2 >= cn[2]) continue;
-                const int s = cb[0][i0] + P.nb[0] * (cb[1][i1] + P.nb[1] * cb[2][i2]);
+            for (int i2 = 0; i2 < 3; ++i2) {
                 const T wgt = cw[0][i0] * cw[1][i1] * cw[2][i2];
-                if (wgt == T(0)) continue;
+                if (wgt == T(0) || nbx >= kMaxBox) continue;
+                const int s = cb[0][i0] + P.nb[0] * (cb[1][i1] + P.nb[1] * cb[2][i2]);
                 const SubDesc& S = subs[s];
                 int64_t li = 0;
-                for (int a = ndim - 1; a >= 0; --a) li = li * S.nw[a] + (g[a] - S.lo[a]);
+#pragma unroll
+                for (int a = 2; a >= 0; --a)
+                    if (a < ndim) li = li * S.nw[a] + (g[a] - S.lo[a]);
 #pragma unroll
                 for (int ib = 0; ib < kMaxBox; ++ib)  // register-resident list: static indices
                     if (ib == nbx) {

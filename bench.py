@@ -39,7 +39,7 @@ METRIC = "RHS solves/sec at 1e-6 rel. L2 (mixed vs plain FP64 GPU DDM); %tensor/
 # solve launches of one step of this workload, from one single-pass ncu capture
 # (profiles/launches_2d-layered-1064sq-64rhs.md), per --prec.  An entry is removed when
 # the kernel changes.
-SOLVE_TRAFFIC_BYTES_PER_LAUNCH = {}
+SOLVE_TRAFFIC_BYTES_PER_LAUNCH = {"f16": 546.8e6}
 UNIT = "RHS/s"
 
 

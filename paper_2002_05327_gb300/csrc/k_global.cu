@@ -85,18 +85,18 @@ void launch_stencil_ff(const DevProblem& P, const Win<double>& g, const double* 
 // b - A u (or -A u without b).  One thread per (grid node, pair of
 // right-hand sides): the node's stencil (float-float, from stencil_ff_kernel)
 // is read once and applied to both in float-float arithmetic on the FP32
-// pipes, their loads issued together.  u and r are complex128 (the caller's
+// pipes, their loads issued together.  The pairs are the fast grid axis, so
+// the blocks of one node range run together and share its stencil and
+// neighbour rows through L2 (node ranges fastest re-read the stencil from DRAM
+// once per pair).  u and r are complex128 (the caller's
 // arrays) or float-float (the Krylov work vectors).  Outside the PML every
 // alpha is 1, so the coefficients are real (their imaginary parts are exact
 // zeros) and each term needs two products, not four.
 constexpr int kAR = 2;  // right-hand sides per thread of the operator product
 template <typename VU, typename VR>
-__global__ void apply_A_kernel(DevProblem P, const float4* __restrict__ stc, const cplx<double>* __restrict__ b,
-                               const VU* __restrict__ u, VR* __restrict__ r, int nrhs) {
-    const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= Ng) return;
-    const int c0 = blockIdx.y * kAR;
+__device__ __forceinline__ void apply_A_node(const DevProblem& P, int64_t Ng, const float4* __restrict__ stc,
+                                             const cplx<double>* __restrict__ b, const VU* __restrict__ u,
+                                             VR* __restrict__ r, int nrhs, int64_t k, int c0) {
     int g[3];
     unflat(k, P.N, g);
     const int npt = 1 + 2 * P.ndim;
@@ -164,10 +164,21 @@ __global__ void apply_A_kernel(DevProblem P, const float4* __restrict__ stc, con
 }
 
 template <typename VU, typename VR>
+__global__ void apply_A_kernel(DevProblem P, const float4* __restrict__ stc, const cplx<double>* __restrict__ b,
+                               const VU* __restrict__ u, VR* __restrict__ r, int nrhs) {
+    const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
+    // node ranges along grid y, strided past the 65535-block limit
+    for (int64_t kb = blockIdx.y; kb * blockDim.x < Ng; kb += gridDim.y) {
+        const int64_t k = kb * blockDim.x + threadIdx.x;
+        if (k < Ng) apply_A_node(P, Ng, stc, b, u, r, nrhs, k, blockIdx.x * kAR);
+    }
+}
+
+template <typename VU, typename VR>
 void launch_apply_A(const DevProblem& P, const float4* stc, const cplx<double>* b, const VU* u, VR* r, int nrhs,
                     cudaStream_t st) {
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
-    dim3 grid((unsigned)((Ng + 255) / 256), (nrhs + kAR - 1) / kAR);
+    dim3 grid((nrhs + kAR - 1) / kAR, (unsigned)std::min<int64_t>((Ng + 255) / 256, 65535));
     apply_A_kernel<VU, VR><<<grid, 256, 0, st>>>(P, stc, b, u, r, nrhs);
 }
 template void launch_apply_A<cplx<double>, cplx<double>>(const DevProblem&, const float4*, const cplx<double>*,

@@ -168,6 +168,8 @@ struct helm_ctx {
     int cap_vec_rhs = 0;
     std::vector<cplx<double>*> gm;  // GMRES vectors (each nrhs*Ng entries of 16 bytes; float-float)
     int gm_rhs = 0;
+    cplx<double>* stage_d[3] = {};     // device staging of the caller's host arrays (grow-only)
+    size_t stage_cap[3] = {};
     float4** vptr_d = nullptr;  // device copies of the V_i and Z_i pointers
     float4** zptr_d = nullptr;
     cplx<double>* small_d = nullptr;  // dots / coefficients
@@ -850,24 +852,32 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const VB* b, VB* U) {
     return HELM_OK;
 }
 
-// ---- host <-> device staging of caller data
+// ---- host <-> device staging of caller data: a caller's host array goes
+// through one of the context's staging buffers (slot 0, 1, 2 in the order of a
+// call's arguments), kept between calls so that no call allocates or frees
+// device memory once they have grown; a device array is used in place.
 struct Staged {
     cplx<double>* ptr = nullptr;
-    bool owned = false;
-    ~Staged() {
-        if (owned && ptr) cudaFree(ptr);
-    }
 };
 
-int stage_in(helm_ctx* c, const void* src, size_t bytes, int mem, Staged& out) {
+int stage_in(helm_ctx* c, const void* src, size_t bytes, int mem, Staged& out, int slot) {
     if (mem == HELM_MEM_DEVICE) {
         out.ptr = (cplx<double>*)src;
-        out.owned = false;
         return HELM_OK;
     }
     if (mem != HELM_MEM_HOST) return fail(HELM_ERR_ARG, "mem must be HELM_MEM_HOST or HELM_MEM_DEVICE");
-    CK(cudaMalloc(&out.ptr, bytes));
-    out.owned = true;
+    if (bytes > c->stage_cap[slot]) {
+        if (c->stage_d[slot]) {
+            CK(cudaFree(c->stage_d[slot]));
+            c->dev_bytes -= c->stage_cap[slot];
+        }
+        c->stage_d[slot] = nullptr;
+        c->stage_cap[slot] = 0;
+        CK(cudaMalloc(&c->stage_d[slot], bytes));
+        c->stage_cap[slot] = bytes;
+        c->dev_bytes += bytes;
+    }
+    out.ptr = c->stage_d[slot];
     if (src) CK(cudaMemcpyAsync(out.ptr, src, bytes, cudaMemcpyHostToDevice, c->stream));
     return HELM_OK;
 }
@@ -1255,8 +1265,8 @@ int helm_apply_ddm(helm_ctx* c, int nrhs, const void* F, void* U, int mem) {
     if (!c->factored) return fail(HELM_ERR_NOT_FACTORED, "call helm_factor first");
     size_t bytes = (size_t)nrhs * c->Ng * 16;
     Staged f, u;
-    TRY(stage_in(c, F, bytes, mem, f));
-    TRY(stage_in(c, mem == HELM_MEM_DEVICE ? U : nullptr, bytes, mem, u));
+    TRY(stage_in(c, F, bytes, mem, f, 0));
+    TRY(stage_in(c, mem == HELM_MEM_DEVICE ? U : nullptr, bytes, mem, u, 1));
     TRY(ensure_bvec(c, nrhs));
     { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_scale_J(c->P, c->gwin, f.ptr, c->bvec, nrhs, false, c->stream); }
     TRY(apply_ddm_dev(c, nrhs, c->bvec, u.ptr));
@@ -1271,8 +1281,8 @@ static int solve_common(helm_ctx* c, int nrhs, const void* F, void* U, int mem, 
     double t0 = now_ms();
     size_t bytes = (size_t)nrhs * c->Ng * 16;
     Staged f, u;
-    TRY(stage_in(c, F, bytes, mem, f));
-    TRY(stage_in(c, mem == HELM_MEM_DEVICE ? U : nullptr, bytes, mem, u));
+    TRY(stage_in(c, F, bytes, mem, f, 0));
+    TRY(stage_in(c, mem == HELM_MEM_DEVICE ? U : nullptr, bytes, mem, u, 1));
     TRY(ensure_bvec(c, nrhs));
     if (adjoint) {
         // A^H lam = g  <=>  A conj(lam) = conj(g)  (A^T = A)
@@ -1308,8 +1318,8 @@ int helm_gradient(helm_ctx* c, int nsrc, const void* U, const void* L, double* g
     if (!c || !U || !L || !grad || nsrc < 1) return fail(HELM_ERR_ARG, "bad argument");
     size_t bytes = (size_t)nsrc * c->Ng * 16;
     Staged u, l;
-    TRY(stage_in(c, U, bytes, mem, u));
-    TRY(stage_in(c, L, bytes, mem, l));
+    TRY(stage_in(c, U, bytes, mem, u, 0));
+    TRY(stage_in(c, L, bytes, mem, l, 1));
     double* gd = grad;
     bool own = false;
     if (mem == HELM_MEM_HOST) {
@@ -1329,9 +1339,9 @@ int helm_residual(helm_ctx* c, int nrhs, const void* F, const void* U, void* R, 
     if (!c || !F || !U || !R || nrhs < 1) return fail(HELM_ERR_ARG, "bad argument");
     size_t bytes = (size_t)nrhs * c->Ng * 16;
     Staged f, u, r;
-    TRY(stage_in(c, F, bytes, mem, f));
-    TRY(stage_in(c, U, bytes, mem, u));
-    TRY(stage_in(c, mem == HELM_MEM_DEVICE ? R : nullptr, bytes, mem, r));
+    TRY(stage_in(c, F, bytes, mem, f, 0));
+    TRY(stage_in(c, U, bytes, mem, u, 1));
+    TRY(stage_in(c, mem == HELM_MEM_DEVICE ? R : nullptr, bytes, mem, r, 2));
     TRY(ensure_bvec(c, nrhs));
     { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_scale_J(c->P, c->gwin, f.ptr, c->bvec, nrhs, false, c->stream); }
     { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_apply_A(c->P, c->stc_d, c->bvec, u.ptr, r.ptr, nrhs, c->stream); }
@@ -1346,7 +1356,7 @@ int helm_subdomain_solve(helm_ctx* c, int s, int nrhs, const void* R, void* U, i
     const int64_t we = S.win_elems;
     size_t bytes = (size_t)nrhs * we * 16;
     Staged r;
-    TRY(stage_in(c, R, bytes, mem, r));
+    TRY(stage_in(c, R, bytes, mem, r, 0));
     // a private buffer [rhs][window] in the working precision
     void* wb = nullptr;
     CK(cudaMalloc(&wb, (size_t)nrhs * we * elem_size(c)));
@@ -1483,7 +1493,7 @@ void helm_destroy(helm_ctx* c) {
                     c->fac, c->err_d, c->tasks_d, c->inc_d, c->gnode_d, c->gblk_d, c->node_buf_d, c->buf,
                     c->bvec,
                     c->small_d, c->partial_d, c->vptr_d, c->zptr_d, c->ascale_d, c->bsrc,
-                    c->stc_d};
+                    c->stc_d, c->stage_d[0], c->stage_d[1], c->stage_d[2]};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     for (auto* p : c->gm) cudaFree(p);

@@ -6,8 +6,9 @@ Workload: the 2D layered seismic-shaped problem -- 1024^2 interior cells
 1.5-4.5 km/s with a +-10 % correlated perturbation, 8 x 8 subdomains
 (box 128, overlap 8, subdomain PML 20), 64 point sources at 20 m depth.
 One step = one helm_solve of all 64 right-hand sides: DDM-preconditioned FP64
-flexible GMRES with complex64 subdomain factors and solves, to a relative
-residual of --rtol.  Factors are computed once, outside the timed steps, and
+flexible GMRES (float-float arithmetic on the FP32 pipes) with complex64
+subdomain factors and FP16 tensor-core solves (--prec tf32 | mixed select the
+other modes), to a relative residual of --rtol.  Factors are computed once, outside the timed steps, and
 reported separately.  Metric: right-hand sides solved per second.
 
 Also reported on the same line: the plain FP64 GPU DDM (complex128 factors and

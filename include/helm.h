@@ -20,7 +20,9 @@
  *
  * Memory: every entry point that takes data pointers also takes `mem`:
  * HELM_MEM_HOST (pageable or pinned host memory; the library copies in and
- * out, synchronously) or HELM_MEM_DEVICE (CUDA device pointers valid in the
+ * out, synchronously, through up to three device staging buffers that the
+ * context keeps between calls -- they only grow, and helm_destroy frees them)
+ * or HELM_MEM_DEVICE (CUDA device pointers valid in the
  * current device's primary context; work is queued on the context's stream
  * and completed before return).  The caller owns every pointer it passes; the
  * library copies what it needs and never keeps a caller pointer.

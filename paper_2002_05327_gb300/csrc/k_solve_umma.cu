@@ -1,5 +1,11 @@
-// Subdomain solves on the 5th-generation tensor cores: tcgen05.mma (kind::tf32)
-// with TMEM accumulators, operands in shared memory fed by the bulk-copy engine.
+// Subdomain solves on the 5th-generation tensor cores: tcgen05.mma (kind::tf32,
+// and kind::f16 with power-of-two scaled operands) with TMEM accumulators,
+// operands in shared memory fed by the bulk-copy engine.  Two kernels:
+//   * solve_twist_kernel (the default): the twisted factors, solved from both
+//     ends toward the middle line by the two CTAs of a cluster, each holding
+//     all rows of the block -- described before its definition below;
+//   * solve_umma_kernel (one-ended): the block rows split over the CTAs of a
+//     cluster, the next right-hand side exchanged every step -- described here.
 //
 // Recurrence (block-Thomas, k_factor.cu): forward y_j = D_j (b_j - a_j y_{j-1}),
 // backward u_j = y_j - D_j (c_j u_{j+1}).  Each block product D_j R is one real

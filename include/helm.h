@@ -114,12 +114,19 @@ typedef struct {
                            2 = tcgen05, one-ended form only */
     int32_t wait_limit; /* bound of every ordinary spin-wait inside the subdomain-solve
                            kernels (a bulk copy, an MMA commit, a peer CTA's handshake),
-                           in polls of the mbarrier: 0 = default (2^22 polls); n > 0 = n polls; -1 = no poll, so the first such wait
-                           gives up at once.  A wait that gives up makes the call return
+                           in polls of the mbarrier: 0 = default (2^22 polls); n > 0 = n
+                           polls; -1 = no poll, so the first such wait gives up at once.  A wait that gives up makes the call return
                            HELM_ERR_TIMEOUT; the kernel stops issuing work, still waits
                            (with the default bound) for the copies and MMAs it has started,
                            frees its tensor memory and exits, so the CUDA context stays
                            usable.  -1 exists for testing callers' handling of that error. */
+    int32_t sweep_order; /* 3D only (Section 4.1): 0 = the order (Sorder3D) of Algorithm
+                           4.1, the 2D order with first +z then -z; 1 = the alternative
+                           order given there, along which the L1 distance to the first
+                           direction never decreases: (+,+,+), (-,+,+), (+,-,+), (+,+,-),
+                           (-,-,+), (-,+,-), (+,-,-), (-,-,-).  The routing rules (4.1,
+                           4.2, smallest usable later sweep) are the same.  Other values
+                           return HELM_ERR_ARG. */
 } helm_config;
 
 typedef struct {

@@ -48,9 +48,18 @@ def beta_hat(t):
 
 
 # ----------------------------------------------------------------------------- sweeps and rules
-def sweep_dirs(ndim):
+# the other 3D order Section 4.1 mentions: the L1 distance of each direction
+# to the first one never decreases along it
+ALT_ORDER_3D = [(1, 1, 1), (-1, 1, 1), (1, -1, 1), (1, 1, -1),
+                (-1, -1, 1), (-1, 1, -1), (1, -1, -1), (-1, -1, -1)]
+
+
+def sweep_dirs(ndim, order=0):
     """Sweep order: (+,+),(-,+),(+,-),(-,-) in 2D (Algorithm 3.1); list
-    (Sorder3D) in 3D (Section 4.1): x flips fastest, then y, then z."""
+    (Sorder3D) in 3D (Section 4.1): x flips fastest, then y, then z.  With
+    order=1 in 3D, the alternative order of Section 4.1 (ALT_ORDER_3D)."""
+    if ndim == 3 and order == 1:
+        return list(ALT_ORDER_3D)
     return [tuple(-1 if (l >> a) & 1 else 1 for a in range(ndim)) for l in range(2 ** ndim)]
 
 
@@ -82,11 +91,11 @@ def opposite_block(d_src, d_gen, d_use):
     return False
 
 
-def route(ndim):
+def route(ndim, order=0):
     """Routing table {(l, d_src): l'} -- the smallest sweep l' >= l that may
     use a source of direction d_src generated in sweep l (Algorithm 3.1 / 4.1),
-    or None if no later sweep may use it."""
-    S = sweep_dirs(ndim)
+    or None if no later sweep may use it; ``order`` as in sweep_dirs."""
+    S = sweep_dirs(ndim, order)
     table = {}
     for l in range(len(S)):
         for d in transfer_dirs(ndim):
@@ -291,16 +300,17 @@ class Partition:
         return U
 
 
-def diagonal_sweep(part: Partition, b, trace=None, nsweeps=None):
+def diagonal_sweep(part: Partition, b, trace=None, nsweeps=None, order=0):
     """Algorithm 3.1 (2D) / 4.1 (3D) applied to the J-scaled source b = J f
     (shape (nrhs, *grid)).  Returns u_DDM on the full grid.
 
     ``trace``, if a dict, receives per (l, I) the local source and solution and
     per (l, I, d) the routed sweep, for invariant tests; ``nsweeps`` stops after
-    the first sweeps (tests of the first sweep only)."""
+    the first sweeps (tests of the first sweep only); ``order`` selects the 3D
+    sweep order (sweep_dirs)."""
     ndim, nb = part.ndim, part.nb
-    S = sweep_dirs(ndim)
-    table = route(ndim)
+    S = sweep_dirs(ndim, order)
+    table = route(ndim, order)
     nrhs = b.shape[0]
     r = {}
     for I, s in part.subs.items():
@@ -371,10 +381,11 @@ class DDMPreconditioner:
         return diagonal_sweep(self.part, b)
 
 
-def ddm_solution(wl, f=None, form="literal"):
-    """u_DDM for source f: Algorithm 3.1/4.1 applied to J f."""
+def ddm_solution(wl, f=None, form="literal", order=0):
+    """u_DDM for source f: Algorithm 3.1/4.1 applied to J f (3D sweep order
+    ``order``, as in sweep_dirs)."""
     f = wl.f if f is None else f
     _, J = global_operator(wl, form)
     part = Partition(wl, form)
     b = f * J.reshape((1,) + f.shape[1:])
-    return diagonal_sweep(part, b)
+    return diagonal_sweep(part, b, order=order)

@@ -283,13 +283,20 @@ int ensure_small(helm_ctx* c, size_t count) {
 }
 
 // ----------------------------------------------------------------------------- routing (Rules 3.1/3.2, 4.1/4.2)
-std::vector<std::array<int, 3>> sweep_dirs(int ndim) {
+// Sweep order: in 2D (+,+), (-,+), (+,-), (-,-) (Algorithm 3.1); in 3D the
+// list (Sorder3D) of Algorithm 4.1 (x flips fastest, then y, then z), or with
+// order 1 the alternative of Section 4.1 whose L1 distance to the first
+// direction never decreases.
+std::vector<std::array<int, 3>> sweep_dirs(int ndim, int order) {
     std::vector<std::array<int, 3>> S;
     for (int l = 0; l < (1 << ndim); ++l) {
         std::array<int, 3> D{0, 0, 0};
         for (int a = 0; a < ndim; ++a) D[a] = ((l >> a) & 1) ? -1 : 1;
         S.push_back(D);
     }
+    if (ndim == 3 && order == 1)
+        S = {{{1, 1, 1}}, {{-1, 1, 1}}, {{1, -1, 1}}, {{1, 1, -1}},
+             {{-1, -1, 1}}, {{-1, 1, -1}}, {{1, -1, -1}}, {{-1, -1, -1}}};
     return S;
 }
 
@@ -446,6 +453,7 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
     if (c->cfg.restart <= 0) c->cfg.restart = 30;
     if (c->cfg.restart > 63) return fail(HELM_ERR_ARG, "restart must be at most 63");
     if (c->cfg.wait_limit < -1) return fail(HELM_ERR_ARG, "wait_limit must be -1, 0 or positive");
+    if (c->cfg.sweep_order != 0 && c->cfg.sweep_order != 1) return fail(HELM_ERR_ARG, "sweep_order must be 0 or 1");
     c->wait_polls = c->cfg.wait_limit == 0    ? kDefaultWaitPolls
                     : c->cfg.wait_limit == -1 ? 0u
                                               : (uint32_t)c->cfg.wait_limit;
@@ -656,7 +664,7 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
     c->fac_bytes = (size_t)fac_elems * (c->prec == HELM_PREC_F64 ? 8 : 4);
 
     // ---- routing and dependency levels of one application of Algorithm 3.1/4.1
-    auto S = sweep_dirs(ndim);
+    auto S = sweep_dirs(ndim, c->cfg.sweep_order);
     auto dirs = transfer_dirs(ndim);
     const int L = c->nsweeps, ns = P.nsub;
     struct Edge {

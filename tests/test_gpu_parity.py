@@ -97,6 +97,23 @@ def test_apply_ddm_matches_algorithm(H, case, prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", [0, 5])
+def test_alternative_3d_sweep_order_matches_algorithm(H, prec):
+    """helm_config.sweep_order = 1 (the second 3D order of Section 4.1) equals
+    the oracle's Algorithm 4.1 in that order; the plain FP64 path also differs
+    from the first order's result, so the option is in effect."""
+    wl = CASES["3d-layered-3x2x2"]()
+    ctx = _ctx(H, wl, prec, sweep_order=1)
+    u = H.helm_apply_ddm(ctx, wl.f)
+    ctx.close()
+    ref = OD.ddm_solution(wl, order=1)
+    assert rel(u, ref) < TOL[prec], rel(u, ref)
+    if prec == 0:
+        assert rel(u, OD.ddm_solution(wl, order=0)) > 1e-6
+    with pytest.raises(H.HelmError):
+        H.helm_setup_workload(wl, sweep_order=2)
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_subdomain_solve_matches_local_direct_solve(H, prec):
     wl = W.small_2d(nx=60, ny=52, nbx=4, nby=3, nrhs=3)

@@ -127,6 +127,32 @@ def test_sweeps_exact_with_untruncated_local_solver(case):
     assert rel(D.additive(part, b), ug) < 1e-12
 
 
+def test_alternative_3d_sweep_order_keeps_the_l1_distance_monotone():
+    """Section 4.1's second 3D order: the same eight directions, the same first
+    one, and the L1 distance of each to the first never decreases."""
+    S0, S1 = D.sweep_dirs(3, 0), D.sweep_dirs(3, 1)
+    assert S1[0] == S0[0] == (1, 1, 1)
+    assert sorted(S1) == sorted(S0)
+    dist = [sum(abs(a - b) for a, b in zip(d, S1[0])) for d in S1]
+    assert dist == sorted(dist)
+    assert D.sweep_dirs(2, 1) == D.sweep_dirs(2, 0)  # 2D has one order
+
+
+def test_alternative_3d_sweep_order_is_exact(monkeypatch):
+    """With the alternative order and the same Rules 4.1/4.2 (smallest usable
+    later sweep), Algorithm 4.1 with untruncated local solves reproduces the
+    global solution to rounding, as with list (Sorder3D); routing it by the
+    first order's table instead breaks that."""
+    wl = W.small_3d(n=(20, 12, 12), nb=(3, 2, 2), pml=4, overlap=2, nrhs=1, medium="layered")
+    ug = H.solve_global(wl)
+    part = D.Partition(wl, ideal=True)
+    b = _bj(wl)
+    assert rel(D.diagonal_sweep(part, b, order=1), ug) < 1e-12
+    route = D.route
+    monkeypatch.setattr(D, "route", lambda ndim, order=0: route(ndim, 0))
+    assert rel(D.diagonal_sweep(part, b, order=1), ug) > 1e-2
+
+
 def test_subdomain_pml_gap_decreases_with_width():
     """Section 5: in constant medium the DDM solution differs from the global
     PML solution only by the truncation of the subdomain PMLs; the gap must

@@ -171,6 +171,18 @@ int helm_apply_ddm(helm_ctx *ctx, int nrhs, const void *F, void *U, int mem);
 int helm_solve(helm_ctx *ctx, int nrhs, const void *F, void *U, int mem, double rtol,
                int maxit, helm_stats *st);
 
+/* The DDM as a stationary iteration, the way Section 5.2.2 runs it (as an
+ * iterative solver rather than a preconditioner, to show the residual decay
+ * of the method itself): u_0 = 0, u_{k+1} = u_k + M (J f - A u_k) with M one
+ * application of Algorithm 3.1/4.1, until the relative residual
+ * |Jf - A u|/|Jf| is <= rtol for every right-hand side or maxit applications.
+ * st->iters and st->applications give the applications made, st->resid the
+ * last residual (max over right-hand sides).  Returns HELM_ERR_NO_CONVERGENCE
+ * (with U and *st written) if maxit is hit.  F, U: complex128
+ * [nrhs][full grid].  st may be NULL. */
+int helm_iterate(helm_ctx *ctx, int nrhs, const void *F, void *U, int mem, double rtol,
+                 int maxit, helm_stats *st);
+
 /* Adjoint solve A^H lambda = g.  A is complex symmetric, so this runs
  * helm_solve on conj(g) with the same factors and DDM and conjugates the
  * result.  G, Lambda: complex128 [nrhs][full grid]. */

@@ -371,6 +371,27 @@ def additive(part: Partition, b):
     return part.assemble_solution(parts, nrhs)
 
 
+def stationary(part: Partition, A, b, iters, order=0):
+    """The DDM as an iterative solver, the way Section 5.2.2 runs it (rather
+    than as a preconditioner): u_0 = 0, u_{k+1} = u_k + M (b - A u_k), with M
+    one application of Algorithm 3.1/4.1 and b = J f.  Returns the iterates
+    u_1 .. u_iters and the relative residuals |b - A u_k| / |b| for
+    k = 0 .. iters (max over right-hand sides)."""
+    nrhs = b.shape[0]
+    bn = np.linalg.norm(b.reshape(nrhs, -1), axis=1)
+    bn[bn == 0] = 1.0
+    u = np.zeros_like(b)
+    us, res = [], []
+    for k in range(iters + 1):
+        r = b - (A @ u.reshape(nrhs, -1).T).T.reshape(b.shape)
+        res.append(float(np.max(np.linalg.norm(r.reshape(nrhs, -1), axis=1) / bn)))
+        if k == iters:
+            break
+        u = u + diagonal_sweep(part, r, order=order)
+        us.append(u)
+    return us, res
+
+
 class DDMPreconditioner:
     """M: J-scaled residual -> correction, one application of Algorithm 3.1/4.1."""
 

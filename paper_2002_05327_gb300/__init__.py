@@ -89,6 +89,9 @@ _SIGS = {
     "helm_solve": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
                                   ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                   ctypes.POINTER(helm_stats)]),
+    "helm_iterate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                                    ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                    ctypes.POINTER(helm_stats)]),
     "helm_adjoint": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p,
                                     ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                     ctypes.POINTER(helm_stats)]),
@@ -263,6 +266,19 @@ def helm_solve(ctx: Context, F, rtol=1e-8, maxit=100, allow_noconv=False):
     rc = lib().helm_solve(ctx.ptr, nr, fp, up, mem, float(rtol), int(maxit), ctypes.byref(st))
     if not (allow_noconv and rc == HELM_ERR_NO_CONVERGENCE):
         _check(rc, "helm_solve")
+    return U, st.as_dict()
+
+
+def helm_iterate(ctx: Context, F, rtol=1e-8, maxit=100, allow_noconv=False):
+    """The DDM as a stationary iteration (helm_iterate): returns U and the stats."""
+    nr = _nrhs(F, ctx)
+    fp, mem, kf = _ptr_mem(F, np.complex128)
+    U = _empty_like(F, tuple(F.shape), np.complex128)
+    up, _, ku = _ptr_mem(U, np.complex128)
+    st = helm_stats()
+    rc = lib().helm_iterate(ctx.ptr, nr, fp, up, mem, float(rtol), int(maxit), ctypes.byref(st))
+    if not (allow_noconv and rc == HELM_ERR_NO_CONVERGENCE):
+        _check(rc, "helm_iterate")
     return U, st.as_dict()
 
 

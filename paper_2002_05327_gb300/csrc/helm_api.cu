@@ -1151,6 +1151,65 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
     return HELM_OK;
 }
 
+// The DDM as a stationary iteration (Section 5.2.2): u_0 = 0,
+// u_{k+1} = u_k + M (b - A u_k).  The residual goes to work vector 0 and the
+// correction M r to work vector 1 (float-float); the solution is updated by
+// the combination kernel with coefficient 1.
+int stationary_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, double rtol, int maxit,
+                   helm_stats* st) {
+    const int64_t Ng = c->Ng;
+    TRY(ensure_gm(c, nrhs, 2));
+    TRY(ensure_small(c, (size_t)2 * nrhs));
+    const int nblk = (int)std::min<int64_t>(256, (Ng + 4095) / 4096);
+    std::vector<cplx<double>> hd(nrhs);
+    auto norms = [&](const auto* v, std::vector<double>& out) -> int {
+        { ProfScope ps_(c, HELM_K_KRYLOV, 2); launch_norms2(v, Ng, nrhs, c->small_d, c->partial_d, nblk, c->stream); }
+        CK(cudaMemcpyAsync(hd.data(), c->small_d, nrhs * 16, cudaMemcpyDeviceToHost, c->stream));
+        CK(cudaStreamSynchronize(c->stream));
+        for (int r = 0; r < nrhs; ++r) out[r] = std::sqrt(std::max(0.0, hd[r].re));
+        return HELM_OK;
+    };
+    CK(cudaMemsetAsync(x, 0, (size_t)nrhs * Ng * 16, c->stream));
+    std::vector<double> bn(nrhs), rn(nrhs);
+    TRY(norms(b, bn));
+    for (auto& v : bn)
+        if (v == 0) v = 1;
+    const std::vector<cplx<double>> one(nrhs, cplx<double>{1.0, 0.0});
+    int apps = 0;
+    double maxres = 0;
+    bool conv = false;
+    while (true) {
+        float4* r = reinterpret_cast<float4*>(c->gm[0]);
+        float4* z = reinterpret_cast<float4*>(c->gm[1]);
+        { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_apply_A(c->P, c->stc_d, b, x, r, nrhs, c->stream); }
+        TRY(norms(r, rn));
+        maxres = 0;
+        for (int q = 0; q < nrhs; ++q) maxres = std::max(maxres, rn[q] / bn[q]);
+        if (c->cfg.verbose) fprintf(stderr, "[helm] iteration %d max rel resid %.3e\n", apps, maxres);
+        if (maxres <= rtol) {
+            conv = true;
+            break;
+        }
+        if (apps >= maxit) break;
+        TRY(apply_ddm_dev(c, nrhs, static_cast<const float4*>(r), z));
+        ++apps;
+        TRY(check_device_error(c));  // a timed-out subdomain solve ends the iteration here
+        CK(cudaMemcpyAsync(c->small_d, one.data(), nrhs * 16, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaMemcpyAsync(c->zptr_d, &z, sizeof(float4*), cudaMemcpyHostToDevice, c->stream));
+        { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_mcombo(x, c->zptr_d, 1, c->small_d, Ng, nrhs, 1.0, c->stream); }
+    }
+    if (st) {
+        st->iters = apps;
+        st->applications = apps;
+        st->resid = maxres;
+        st->levels = (int)c->levels.size();
+        st->solves = c->nsolves;
+    }
+    CK(cudaGetLastError());
+    if (!conv) return fail(HELM_ERR_NO_CONVERGENCE, "the stationary iteration reached maxit");
+    return HELM_OK;
+}
+
 double now_ms() {
     return std::chrono::duration<double, std::milli>(
                std::chrono::steady_clock::now().time_since_epoch())
@@ -1282,7 +1341,7 @@ int helm_apply_ddm(helm_ctx* c, int nrhs, const void* F, void* U, int mem) {
 }
 
 static int solve_common(helm_ctx* c, int nrhs, const void* F, void* U, int mem, double rtol,
-                        int maxit, helm_stats* st, bool adjoint) {
+                        int maxit, helm_stats* st, bool adjoint, bool stationary = false) {
     if (!c || !F || !U || nrhs < 1 || !(rtol > 0) || maxit < 1)
         return fail(HELM_ERR_ARG, "bad argument");
     if (!c->factored) return fail(HELM_ERR_NOT_FACTORED, "call helm_factor first");
@@ -1299,7 +1358,8 @@ static int solve_common(helm_ctx* c, int nrhs, const void* F, void* U, int mem, 
     } else {
         { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_scale_J(c->P, c->gwin, f.ptr, c->bvec, nrhs, false, c->stream); }
     }
-    int rc = gmres_dev(c, nrhs, c->bvec, u.ptr, rtol, maxit, st);
+    int rc = stationary ? stationary_dev(c, nrhs, c->bvec, u.ptr, rtol, maxit, st)
+                        : gmres_dev(c, nrhs, c->bvec, u.ptr, rtol, maxit, st);
     if (rc != HELM_OK && rc != HELM_ERR_NO_CONVERGENCE) return rc;
     std::string msg = g_last_error;
     if (adjoint) launch_conj(u.ptr, (int64_t)nrhs * c->Ng, c->stream);
@@ -1315,6 +1375,11 @@ static int solve_common(helm_ctx* c, int nrhs, const void* F, void* U, int mem, 
 int helm_solve(helm_ctx* c, int nrhs, const void* F, void* U, int mem, double rtol, int maxit,
                helm_stats* st) {
     return solve_common(c, nrhs, F, U, mem, rtol, maxit, st, false);
+}
+
+int helm_iterate(helm_ctx* c, int nrhs, const void* F, void* U, int mem, double rtol, int maxit,
+                 helm_stats* st) {
+    return solve_common(c, nrhs, F, U, mem, rtol, maxit, st, false, true);
 }
 
 int helm_adjoint(helm_ctx* c, int nrhs, const void* G, void* L, int mem, double rtol, int maxit,

@@ -156,6 +156,27 @@ def test_gmres_reaches_global_solution(H, prec):
     ctx.close()
 
 
+def test_stationary_iteration_matches_algorithm(H):
+    """helm_iterate, the DDM as an iterative solver (Section 5.2.2): after three
+    steps the FP64 iterate equals the oracle's u_3 and its residual; with FP16
+    subdomain solves the iteration converges to the global solution."""
+    wl = W.small_2d(nx=64, ny=56, nbx=3, nby=3, pml=10, overlap=4, sub_pml=10, nrhs=3)
+    A, J = OH.global_operator(wl)
+    b = wl.f * J.reshape((1,) + wl.f.shape[1:])
+    us, res = OD.stationary(OD.Partition(wl), A, b, 3)
+    ctx = _ctx(H, wl, 0)
+    u, st = H.helm_iterate(ctx, wl.f, rtol=1e-30, maxit=3, allow_noconv=True)
+    ctx.close()
+    assert st["applications"] == 3
+    assert rel(u, us[-1]) < 1e-10, rel(u, us[-1])
+    assert abs(st["resid"] - res[-1]) <= 1e-3 * res[-1], (st["resid"], res[-1])
+    ctx = _ctx(H, wl, 5)
+    u, st = H.helm_iterate(ctx, wl.f, rtol=1e-10, maxit=60)
+    ctx.close()
+    assert rel(u, OH.solve_global(wl)) < 1e-6
+    assert st["resid"] <= 1e-10
+
+
 def test_residual_matches_operator(H):
     wl = W.small_3d(n=(12, 10, 9), nb=(2, 2, 1), pml=4, overlap=2, sub_pml=3, nrhs=2,
                     medium="layered")

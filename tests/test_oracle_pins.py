@@ -169,17 +169,21 @@ def test_subdomain_pml_gap_decreases_with_width():
 
 
 def _two_layer_gap(wl, iters):
+    """Error of the stationary DDM iterates u_1 .. u_iters (Section 5.2.2)."""
     A, J = H.global_operator(wl)
     ug = H.solve_global(wl)
-    b = _bj(wl)
-    part = D.Partition(wl)
-    u = np.zeros_like(b)
-    out = []
-    for _ in range(iters):
-        r = b - (A @ u.reshape(u.shape[0], -1).T).T.reshape(b.shape)
-        u = u + D.diagonal_sweep(part, r)
-        out.append(rel(u, ug))
-    return out
+    us, _ = D.stationary(D.Partition(wl), A, _bj(wl), iters)
+    return [rel(u, ug) for u in us]
+
+
+def test_stationary_iteration_is_exact_after_one_step_with_untruncated_local_solves():
+    """With untruncated local solves M = A^-1 (Theorem 3.1), so one step of
+    the stationary iteration leaves only rounding in the residual."""
+    wl = W.small_2d(nrhs=2)
+    A, J = H.global_operator(wl)
+    _, res = D.stationary(D.Partition(wl, ideal=True), A, _bj(wl), 1)
+    assert res[0] == pytest.approx(1.0)
+    assert res[1] < 1e-12
 
 
 def test_two_layer_2x2_one_iteration():

@@ -153,6 +153,30 @@ def test_alternative_3d_sweep_order_is_exact(monkeypatch):
     assert rel(D.diagonal_sweep(part, b, order=1), ug) > 1e-2
 
 
+def _tab_iter_const():
+    rows = []
+    for line in open(os.path.join(GOLDEN, "tab_iter_const.txt")):
+        if line.strip() and not line.startswith("#"):
+            cells, nb, freq, iters = (int(v) for v in line.split())
+            rows.append((cells, nb, freq, iters))
+    return rows
+
+
+@pytest.mark.parametrize("row", [r for r in _tab_iter_const() if r[0] <= 1200], ids=lambda r: f"{r[0]}sq")
+def test_gmres_iterations_match_the_constant_medium_table(row):
+    """Section 5.2.1, Table tab:iter_const: with the DDM (Algorithm 3.1) as the
+    preconditioner, GMRES reaches a relative residual of 1e-6 in the printed
+    number of iterations (600^2 on 2x2 and 1200^2 on 4x4 subdomains of 300^2
+    cells, 30-cell PML, four point sources)."""
+    cells, nb, freq, iters = row
+    wl = W.iter_const_2d(cells, nb, freq)
+    A, J = H.global_operator(wl)
+    b = _bj(wl)
+    Ax = lambda x: (A @ x.reshape(x.shape[0], -1).T).T.reshape(x.shape)
+    _, info = K.gmres(Ax, b, D.DDMPreconditioner(wl), rtol=1e-6, restart=30, maxit=20)
+    assert int(info["iters"][0]) == iters, info["history"]
+
+
 def test_subdomain_pml_gap_decreases_with_width():
     """Section 5: in constant medium the DDM solution differs from the global
     PML solution only by the truncation of the subdomain PMLs; the gap must

@@ -224,6 +224,22 @@ def config(k: int, with_sources: bool = True, src: Sequence[int] = None) -> Work
     raise ValueError(f"unknown config {k}")
 
 
+def iter_const_2d(cells: int, nb: int, freq: float, pml: int = 30, overlap: int = 8) -> Workload:
+    """The constant-medium scaling problems of Section 5.2.1: the unit square
+    (c = 1) with ``cells`` x ``cells`` cells in ``nb`` x ``nb`` equal subdomains,
+    omega = 2 pi freq, a PML of ``pml`` cells (global and subdomain) and one
+    right-hand side made of four discrete deltas at the quarter points
+    (1/4, 1/4), (1/4, 3/4), (3/4, 1/4), (3/4, 3/4), each at its nearest node.
+    The overlap d is not stated there (8 cells, as for the other workloads)."""
+    n = (cells, cells)
+    h = 1.0 / cells
+    m = constant_medium(n, pml)
+    idx = [int(round(q / h - 0.5)) + pml for q in (0.25, 0.75)]
+    f = point_sources(n, pml, h, [(ix, iy) for ix in idx for iy in idx]).sum(axis=0, keepdims=True)
+    return Workload(f"2d-const-{cells}sq-{nb}x{nb}-iter", 2, n, h, 2 * np.pi * freq, pml, 50.0, 2,
+                    (nb, nb), (uniform_cuts(cells, nb), uniform_cuts(cells, nb)), overlap, pml, m, f)
+
+
 def small_2d(nx=48, ny=40, nbx=3, nby=2, pml=8, overlap=4, sub_pml=8, nrhs=2,
              medium="layered", omega=None, seed=7, sigma0=50.0) -> Workload:
     """A small 2D case (oracle runs in well under a second) spanning several

@@ -268,7 +268,7 @@ def test_routing_3d_sorder_and_first_sweep():
     assert tab[(0, (1, 1, -1))] == 4
 
 
-def _single_source_trace(wl, box, nsweeps=None):
+def _single_source_trace(wl, box, nsweeps=None, order=0):
     """Algorithm 3.1/4.1 with untruncated local solves on a source confined to
     one box; returns the trace."""
     part = D.Partition(wl, ideal=True)
@@ -279,7 +279,7 @@ def _single_source_trace(wl, box, nsweeps=None):
     mask[sl] = 1.0
     b = b * mask[None]
     trace = {}
-    D.diagonal_sweep(part, b, trace, nsweeps)
+    D.diagonal_sweep(part, b, trace, nsweeps, order=order)
     return part, trace
 
 
@@ -307,6 +307,24 @@ def test_sweep_supports_and_first_steps_2d():
             if nz:
                 steps.append(D.front_index(I, part.nb, S[l]) + 1)
         assert min(steps) == first[l]
+
+
+@pytest.mark.parametrize("order", [0, 1])
+def test_sweep_supports_3d(order):
+    """Section 4.2, the extended octants (octa3D): for a source in
+    Omega_{i0,j0,k0}, the sweep along direction d is non-zero exactly on the
+    octant of d -- box indices >= i0 along an axis where d is +1 and < i0 where
+    it is -1 -- for both sweep orders of Section 4.1."""
+    n, P = (18, 18, 18), 4
+    wl = W.small_3d(n=n, nb=(3, 3, 3), pml=P, overlap=2, sub_pml=3, nrhs=1)
+    wl = dataclasses.replace(wl, f=W.point_sources(n, P, wl.h, [(P + 9, P + 9, P + 9)]))
+    part, tr = _single_source_trace(wl, (1, 1, 1), order=order)
+    peak = max(np.abs(v[1]).max() for k, v in tr.items() if len(k) == 2)
+    for l, d in enumerate(D.sweep_dirs(3, order)):
+        for I in part.subs:
+            nz = np.abs(tr[(l, I)][1]).max() > 1e-12 * peak
+            inside = all((i >= 1) if s > 0 else (i < 1) for i, s in zip(I, d))
+            assert nz == inside, (order, l, d, I)
 
 
 def _outgoing_counts(wl, origin):

@@ -12,10 +12,11 @@ other modes), to a relative residual of --rtol.  Factors are computed once, outs
 reported separately.  Metric: right-hand sides solved per second.
 
 Also reported on the same line: the plain FP64 GPU DDM (complex128 factors and
-solves, same algorithm), the roofline of the dominant kernel (subdomain
-solve) from CUDA events on the library's stream, SM clocks sampled during the
-timed region, an end-to-end figure through the C ABI with host buffers, and
-the CPU oracle timed on a bounded sample (rank 0 only).
+solves, same algorithm; single-GPU runs), the roofline of the dominant kernel
+(subdomain solve) from CUDA events on the library's stream, SM clocks sampled
+during the timed region, an end-to-end figure through the C ABI with host
+buffers (slowest replica), and the CPU oracle timed on a bounded sample
+(rank 0 of a single-GPU run).
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 For N > 1 run under torch.distributed.run; every rank solves its own copy of
@@ -304,7 +305,7 @@ def main():
         t = time.time()
         for _ in range(args.steps):
             host_solve()
-        e2e_ms = (time.time() - t) * 1e3 / args.steps
+        e2e_ms = job_ms((time.time() - t) * 1e3 / args.steps, world, dev)  # slowest replica
         e2e = {"value": world * nrhs / (e2e_ms / 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(Fh.numel() * 16), "d2h_bytes_per_step": int(Uh.numel() * 16),
                "ms_per_step": e2e_ms}
@@ -313,9 +314,9 @@ def main():
         Ucheck = U.cpu().numpy()
     ctx.close()
 
-    # ---------------- plain FP64 GPU DDM, same algorithm
+    # ---------------- plain FP64 GPU DDM, same algorithm (the comparator; N = 1 only)
     fp64 = None
-    if not args.no_fp64:
+    if not args.no_fp64 and world == 1:
         c64 = H.helm_setup_workload(wl, precision=H.HELM_PREC_F64, stream=stream)
         t0 = time.time()
         H.helm_factor(c64)
@@ -336,7 +337,7 @@ def main():
 
     if rank != 0:
         return
-    cpu = None if args.no_cpu else cpu_oracle_sample(wl, apps)
+    cpu = None if (args.no_cpu or world > 1) else cpu_oracle_sample(wl, apps)  # rank 0 at N = 1 only
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

@@ -167,7 +167,10 @@ def test_gmres_iterations_match_the_constant_medium_table(row):
     """Section 5.2.1, Table tab:iter_const: with the DDM (Algorithm 3.1) as the
     preconditioner, GMRES reaches a relative residual of 1e-6 in the printed
     number of iterations (600^2 on 2x2 and 1200^2 on 4x4 subdomains of 300^2
-    cells, 30-cell PML, four point sources)."""
+    cells, 30-cell PML, four point sources).  The 2400^2 8x8 row, run once
+    outside the suite, needs 2 iterations where the table prints 3: the
+    paper's PML profile and overlap are not fully given, and the PML read
+    here absorbs more strongly."""
     cells, nb, freq, iters = row
     wl = W.iter_const_2d(cells, nb, freq)
     A, J = H.global_operator(wl)

@@ -38,9 +38,9 @@ sys.path.insert(0, ROOT)
 
 METRIC = "RHS solves/sec at 1e-6 rel. L2 (mixed vs plain FP64 GPU DDM); %tensor/HBM roofline"
 # DRAM bytes (read + write) per launch of the tensor-core solve kernel, averaged over the
-# solve launches of one step of this workload, from one single-pass ncu capture
-# (profiles/launches_2d-layered-1064sq-64rhs.md), per --prec.  An entry is removed when
-# the kernel changes.
+# solve launches of one step of this workload, from one single-pass ncu capture of the
+# bench command's launch list (dram__bytes_read.sum + dram__bytes_write.sum), per --prec.
+# An entry is removed when the kernel changes.
 SOLVE_TRAFFIC_BYTES_PER_LAUNCH = {"f16": 546.8e6}
 UNIT = "RHS/s"
 

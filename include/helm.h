@@ -127,6 +127,12 @@ typedef struct {
                            (-,-,+), (-,+,-), (+,-,-), (-,-,-).  The routing rules (4.1,
                            4.2, smallest usable later sweep) are the same.  Other values
                            return HELM_ERR_ARG. */
+    int64_t max_device_bytes; /* cap on the device memory the context may hold (its own
+                           allocations: coefficients, stencil, factors, work and staging
+                           buffers); 0 = no cap.  An allocation that would go beyond it is
+                           refused with HELM_ERR_OOM before cudaMalloc is called, and
+                           helm_setup refuses a problem whose grid arrays alone exceed it
+                           before touching the device. */
 } helm_config;
 
 typedef struct {
@@ -140,7 +146,8 @@ typedef struct {
 } helm_stats;
 
 /* Create a context: copy m (squared slowness 1/c^2, float64, full grid,
- * host pointer), build the PML coefficients (Eq. 2.1-2.3), the subdomain
+ * host pointer; a NaN or infinite entry returns HELM_ERR_NUMERIC before any
+ * device work), build the PML coefficients (Eq. 2.1-2.3), the subdomain
  * windows (Section 2.1), the routing table of transferred sources by Rules
  * 3.1/3.2 (2D) or 4.1/4.2 (3D) with the smallest-usable-sweep rule of
  * Algorithm 3.1/4.1, and the dependency levels of one sweep application.
@@ -211,15 +218,21 @@ int helm_subdomain_solve(helm_ctx *ctx, int s, int nrhs, const void *R, void *U,
  * that has reserved all device memory up front).  The paper has no
  * counterpart; this is a property of the library, not of the method.
  * R and U are DEVICE pointers (complex128 [nrhs][window]) that the caller
- * owns; nothing is allocated or freed.  The working buffer lives in one
- * static device array of 64 MiB that every GPU loading the library holds
- * until exit: nrhs times the window size times 8 bytes (complex64 context)
- * or 16 bytes (complex128 context) must fit in 64 MiB - 256 bytes, else
- * HELM_ERR_ARG with the sizes in helm_last_error().  The first call on a
- * device looks up that array's device address (set-up work): make it before
- * any stream capture.  Calls share the array and leave its contents behind;
- * calls whose GPU work overlaps race on it.  Synchronises the context's
- * stream before returning. */
+ * owns; nothing is allocated or freed.  The solve runs on the kernel that
+ * helm_subdomain_solve uses for the context's precision (the SIMT solve for
+ * HELM_PREC_F64 and HELM_PREC_MIXED, the tensor-core solves for
+ * HELM_PREC_TF32 and HELM_PREC_F16), so both entry points give the same
+ * answer.  The working buffer lives in one static device array of 64 MiB that
+ * every GPU loading the library holds until exit: nrhs times the window size
+ * times 8 bytes (complex64 context) or 16 bytes (complex128 context) must fit
+ * in 64 MiB - 256 bytes, else HELM_ERR_ARG with the sizes in
+ * helm_last_error().  The current device must be the one that was current at
+ * helm_setup, else HELM_ERR_ARG.  The first call on a device looks up that
+ * array's device address (set-up work): make it before any stream capture;
+ * after cudaDeviceReset the looked-up address is stale, so do not call this
+ * again in that process.  Calls share the array and leave its contents
+ * behind; calls whose GPU work overlaps race on it.  Synchronises the
+ * context's stream before returning. */
 int helm_subdomain_solve_noalloc(helm_ctx *ctx, int s, int nrhs, const void *R, void *U);
 
 /* Window of subdomain s: lo[3], hi[3] full-grid node ranges (hi exclusive). */

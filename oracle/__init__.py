@@ -18,6 +18,6 @@ equation"):
   * ``krylov``     -- right-preconditioned restarted GMRES in float64 (Remark 1).
   * ``adjoint``    -- adjoint solve and the receiver-misfit gradient w.r.t. m.
 
-Readings of the paper where it is silent or garbled are listed in the design doc and
-restated at the point of use.
+Where the paper is silent or garbled, the reading taken is stated at the
+point of use.
 """

@@ -50,7 +50,7 @@ class helm_config(ctypes.Structure):
                 ("restart", ctypes.c_int32), ("verbose", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("profile", ctypes.c_int32),
                 ("tc_kernel", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
-                ("sweep_order", ctypes.c_int32)]
+                ("sweep_order", ctypes.c_int32), ("max_device_bytes", ctypes.c_int64)]
 
 
 KERNEL_CLASSES = ("factor", "solve", "gather", "assemble", "krylov")
@@ -200,7 +200,7 @@ class Context:
 def helm_setup(ndim, n, h, omega, m, pml_width, sigma0, nb, overlap, power=2,
                form=HELM_PML_LITERAL, cuts=None, sub_pml=0, precision=HELM_PREC_MIXED,
                rhs_panel=0, restart=30, verbose=0, stream=None, profile=0,
-               tc_kernel=0, wait_limit=0, sweep_order=0) -> Context:
+               tc_kernel=0, wait_limit=0, sweep_order=0, max_device_bytes=0) -> Context:
     L = lib()
     nn = (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
     m = np.ascontiguousarray(m, dtype=np.float64)
@@ -219,7 +219,7 @@ def helm_setup(ndim, n, h, omega, m, pml_width, sigma0, nb, overlap, power=2,
     part.sub_pml = int(sub_pml)
     cfg = helm_config(int(precision), int(rhs_panel), int(restart), int(verbose),
                       ctypes.c_void_p(stream) if stream else None, int(profile), int(tc_kernel),
-                      int(wait_limit), int(sweep_order))
+                      int(wait_limit), int(sweep_order), int(max_device_bytes))
     out = ctypes.c_void_p()
     _check(L.helm_setup(ctypes.byref(out), int(ndim), nn, float(h), float(omega),
                         m.ctypes.data_as(ctypes.c_void_p), ctypes.byref(pml), ctypes.byref(part),
@@ -339,6 +339,10 @@ def helm_subdomain_solve_noalloc(ctx: Context, s, R):
     (the output tensor is allocated here, by torch, before the call)."""
     if not _is_torch(R):
         raise TypeError("helm_subdomain_solve_noalloc takes CUDA tensors")
+    lo, hi = helm_window_info(ctx, s)
+    shape = tuple(reversed([h - l for l, h in zip(lo, hi)]))
+    if tuple(R.shape[1:]) != shape:
+        raise ValueError(f"expected [nrhs, {shape}], got {tuple(R.shape)}")
     rp, _, kr = _ptr_mem(R, np.complex128)
     U = _empty_like(R, tuple(R.shape), np.complex128)
     up, _, ku = _ptr_mem(U, np.complex128)

@@ -76,19 +76,6 @@ double beta_hat(double t) {
     return 1.0 - t * t * t * (10.0 - 15.0 * t + 6.0 * t * t);
 }
 
-template <typename T>
-T* dalloc(size_t count, int* rc) {
-    void* p = nullptr;
-    if (count == 0) count = 1;
-    cudaError_t e = cudaMalloc(&p, count * sizeof(T));
-    if (e != cudaSuccess) {
-        *rc = fail(HELM_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
-        return nullptr;
-    }
-    *rc = HELM_OK;
-    return static_cast<T*>(p);
-}
-
 }  // namespace
 
 // ----------------------------------------------------------------------------- context
@@ -100,6 +87,7 @@ struct helm_ctx {
     helm_config cfg{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    int device = -1;                   // the device current at helm_setup
     int prec = HELM_PREC_MIXED;
     int nsweeps = 0;
 
@@ -189,6 +177,22 @@ struct helm_ctx {
 
 namespace {
 
+// Every device allocation of a context goes through here: it is refused with
+// HELM_ERR_OOM (before cudaMalloc is called) when it would take the context's
+// device bytes beyond cfg.max_device_bytes, if that is set.
+int ctx_malloc(helm_ctx* c, void** p, size_t bytes) {
+    const size_t cap = c->cfg.max_device_bytes > 0 ? (size_t)c->cfg.max_device_bytes : 0;
+    if (cap && c->dev_bytes + bytes > cap)
+        return fail(HELM_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes beyond the context's cap of " +
+                                      std::to_string(cap) + " bytes (" + std::to_string(c->dev_bytes) + " in use)");
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 1);
+    if (e != cudaSuccess)
+        return fail(e == cudaErrorMemoryAllocation ? HELM_ERR_OOM : HELM_ERR_CUDA,
+                    std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    return HELM_OK;
+}
+#define CKM(ptr, bytes) TRY(ctx_malloc(c, (void**)(ptr), (bytes)))
+
 size_t elem_size(const helm_ctx* c) { return c->prec == HELM_PREC_F64 ? 16 : 8; }
 
 cudaEvent_t pool_event(helm_ctx* c) {
@@ -247,8 +251,8 @@ int ensure_buffers(helm_ctx* c, int nrhs) {
         c->buf = c->bsrc = nullptr;
     }
     size_t bytes = (size_t)nrhs * c->buf_per_rhs * elem_size(c);
-    CK(cudaMalloc(&c->buf, bytes));
-    CK(cudaMalloc(&c->bsrc, bytes));
+    CKM(&c->buf, bytes);
+    CKM(&c->bsrc, bytes);
     CK(cudaMemsetAsync(c->bsrc, 0, bytes, c->stream));  // the gather writes only its fixed node set
     c->dev_bytes += 2 * bytes;
     c->cap_rhs = nrhs;
@@ -262,7 +266,7 @@ int ensure_bvec(helm_ctx* c, int nrhs) {
         c->dev_bytes -= (size_t)c->cap_vec_rhs * c->Ng * 16;
         c->bvec = nullptr;
     }
-    CK(cudaMalloc(&c->bvec, (size_t)nrhs * c->Ng * 16));
+    CKM(&c->bvec, (size_t)nrhs * c->Ng * 16);
     c->dev_bytes += (size_t)nrhs * c->Ng * 16;
     c->cap_vec_rhs = nrhs;
     return HELM_OK;
@@ -272,11 +276,11 @@ int ensure_small(helm_ctx* c, size_t count) {
     if (count <= c->small_cap) return HELM_OK;
     if (c->small_d) cudaFree(c->small_d);
     if (c->partial_d) cudaFree(c->partial_d);
-    CK(cudaMalloc(&c->small_d, count * sizeof(cplx<double>)));
-    CK(cudaMalloc(&c->partial_d, count * 256 * sizeof(cplx<double>)));  // <= 256 block partials per output
+    CKM(&c->small_d, count * sizeof(cplx<double>));
+    CKM(&c->partial_d, count * 256 * sizeof(cplx<double>));  // <= 256 block partials per output
     if (!c->vptr_d) {
-        CK(cudaMalloc(&c->vptr_d, 64 * sizeof(void*)));
-        CK(cudaMalloc(&c->zptr_d, 64 * sizeof(void*)));
+        CKM(&c->vptr_d, 64 * sizeof(void*));
+        CKM(&c->zptr_d, 64 * sizeof(void*));
     }
     c->small_cap = count;
     return HELM_OK;
@@ -351,7 +355,7 @@ void fill_window_alpha(const AxisP& ax, const helm_pml& pml, double omega, std::
 
 template <typename T>
 int upload(T** dst, const void* src, size_t bytes, helm_ctx* c) {
-    CK(cudaMalloc((void**)dst, bytes ? bytes : 1));
+    CKM(dst, bytes);
     if (bytes) CK(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
     c->dev_bytes += bytes;
     return HELM_OK;
@@ -475,7 +479,21 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
     c->Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
     P.nsub = P.nb[0] * P.nb[1] * P.nb[2];
     c->nsweeps = 1 << ndim;
+    // host-side checks before any device work: the medium, and the device-memory cap
+    // against the grid arrays setup allocates (m in float64 and float32, the stencil)
+    for (int64_t i = 0; i < c->Ng; ++i)
+        if (!std::isfinite(m[i]))
+            return fail(HELM_ERR_NUMERIC, "m has a non-finite value at full-grid index " + std::to_string(i));
+    if (c->cfg.max_device_bytes < 0) return fail(HELM_ERR_ARG, "max_device_bytes must be >= 0");
+    {
+        const double grid_bytes = (double)c->Ng * (8.0 + 4.0 + (1 + 2 * ndim) * 16.0);
+        if (c->cfg.max_device_bytes > 0 && grid_bytes > (double)c->cfg.max_device_bytes)
+            return fail(HELM_ERR_OOM, "the grid arrays need " + std::to_string((int64_t)grid_bytes) +
+                                          " bytes, beyond the context's cap of " +
+                                          std::to_string(c->cfg.max_device_bytes) + " bytes");
+    }
 
+    CK(cudaGetDevice(&c->device));
     if (c->cfg.stream) {
         c->stream = (cudaStream_t)c->cfg.stream;
     } else {
@@ -519,7 +537,7 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
     // ---- the global operator's stencil, once (operator products, residuals)
     {
         const size_t bytes = (size_t)c->Ng * (1 + 2 * ndim) * sizeof(float4);
-        CK(cudaMalloc(&c->stc_d, bytes));
+        CKM(&c->stc_d, bytes);
         c->dev_bytes += bytes;
         launch_stencil_ff(P, c->gwin, c->m64, c->stc_d, c->stream);
         CK(cudaGetLastError());
@@ -763,7 +781,7 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
     TRY(upload(&c->inc_d, inc_all.data(), inc_all.size() * sizeof(Incoming), c));
     TRY(build_gather_list(c, all_tasks, inc_all));
     TRY(upload(&c->node_buf_d, c->node_buf_h.data(), c->node_buf_h.size() * 8, c));
-    CK(cudaMalloc(&c->err_d, sizeof(int)));
+    CKM(&c->err_d, sizeof(int));
     return HELM_OK;
 }
 
@@ -881,7 +899,7 @@ int stage_in(helm_ctx* c, const void* src, size_t bytes, int mem, Staged& out, i
         }
         c->stage_d[slot] = nullptr;
         c->stage_cap[slot] = 0;
-        CK(cudaMalloc(&c->stage_d[slot], bytes));
+        CKM(&c->stage_d[slot], bytes);
         c->stage_cap[slot] = bytes;
         c->dev_bytes += bytes;
     }
@@ -919,7 +937,7 @@ int ensure_gm(helm_ctx* c, int nrhs, int count) {
     }
     while ((int)c->gm.size() < count) {
         cplx<double>* p = nullptr;
-        CK(cudaMalloc(&p, (size_t)c->gm_rhs * c->Ng * 16));
+        CKM(&p, (size_t)c->gm_rhs * c->Ng * 16);
         c->dev_bytes += (size_t)c->gm_rhs * c->Ng * 16;
         c->gm.push_back(p);
     }
@@ -1210,6 +1228,39 @@ int stationary_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x
     return HELM_OK;
 }
 
+// The subdomain solve of one task (device descriptor `task`, sweep 0) in place
+// on the window buffer wb ([nrhs][window] in the working precision, local
+// sources and solution in the same array), with the kernel the context's
+// precision selects -- the same choice the DDM application makes.  Queued on
+// the context's stream; allocates nothing.
+void launch_one_subdomain_solve(helm_ctx* c, const Task* task, int nrhs, void* wb, int64_t we) {
+    const int panel = auto_panel(c, nrhs);
+    const DevStatus ds{c->err_d, c->wait_polls};
+    if (c->prec == HELM_PREC_F64) {
+        auto* b = static_cast<cplx<double>*>(wb);
+        launch_solve<double>(task, 1, c->subs_d, c->nbp_max, nrhs, panel, static_cast<const double*>(c->fac),
+                             c->Pv64, c->inva64, b, b, we, ds, c->stream);
+        return;
+    }
+    auto* b = static_cast<cplx<float>*>(wb);
+    if (c->prec == HELM_PREC_TF32 && c->umma_twist)
+        launch_solve_twist(task, 1, c->subs_d, c->umma_nblk, c->umma_lines, nrhs, c->ufac, c->ufac_off, c->ascale_d,
+                           c->f16, c->Pv32, c->inva32, b, b, we, ds, c->stream);
+    else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
+        launch_solve_umma(task, 1, c->subs_d, c->umma_nblk, nrhs, panel, static_cast<const float*>(c->ufac),
+                          c->ufac_off, c->Pv32, c->inva32, b, b, we, ds, c->stream);
+    else if (c->prec == HELM_PREC_TF32)
+        launch_solve_tc(task, 1, c->subs_d, c->nbp_max, nrhs, panel, static_cast<const float*>(c->fac), c->Pv32,
+                        c->inva32, b, b, we, ds, c->stream);
+    else
+        launch_solve<float>(task, 1, c->subs_d, c->nbp_max, nrhs, panel, static_cast<const float*>(c->fac),
+                            c->Pv32, c->inva32, b, b, we, ds, c->stream);
+}
+
+void noalloc_solve_cb(void* ctx, const Task* task, int nrhs, void* wb, int64_t we) {
+    launch_one_subdomain_solve(static_cast<helm_ctx*>(ctx), task, nrhs, wb, we);
+}
+
 double now_ms() {
     return std::chrono::duration<double, std::milli>(
                std::chrono::steady_clock::now().time_since_epoch())
@@ -1243,7 +1294,7 @@ int helm_factor(helm_ctx* c) {
     if (c->factored) return HELM_OK;
     double t0 = now_ms();
     if (!c->fac) {
-        CK(cudaMalloc(&c->fac, c->fac_bytes));
+        CKM(&c->fac, c->fac_bytes);
         c->dev_bytes += c->fac_bytes;
     }
     CK(cudaMemsetAsync(c->fac, 0, c->fac_bytes, c->stream));
@@ -1273,7 +1324,7 @@ int helm_factor(helm_ctx* c) {
         if (twist) {
             // the far half of every subdomain's lines, eliminated from the far end
             // (before the standard factors are rounded: the middle block uses one)
-            CK(cudaMalloc(&fac2, c->fac_bytes));
+            CKM(&fac2, c->fac_bytes);
             launch_factor_twist_f32(c->subs_d, c->P.nsub, c->nbp_max, c->P, c->m32, c->an32, c->af32,
                                     static_cast<const float*>(c->fac), fac2, c->err_d, c->stream);
         }
@@ -1294,13 +1345,13 @@ int helm_factor(helm_ctx* c) {
                 max_lines = std::max(max_lines, S.nlines);
             }
             if (!c->ufac) {
-                CK(cudaMalloc(&c->ufac, (size_t)tot));
+                CKM(&c->ufac, (size_t)tot);
                 c->dev_bytes += (size_t)tot;
                 TRY(upload(&c->ufac_off, off.data(), off.size() * sizeof(int64_t), c));
             }
             if (f16) {
                 if (!c->ascale_d) {
-                    CK(cudaMalloc(&c->ascale_d, c->inva_count * sizeof(int)));
+                    CKM(&c->ascale_d, c->inva_count * sizeof(int));
                     c->dev_bytes += c->inva_count * sizeof(int);
                 }
                 launch_line_scales(c->subs_d, c->P.nsub, max_lines, static_cast<const float*>(c->fac), fac2,
@@ -1396,7 +1447,7 @@ int helm_gradient(helm_ctx* c, int nsrc, const void* U, const void* L, double* g
     double* gd = grad;
     bool own = false;
     if (mem == HELM_MEM_HOST) {
-        CK(cudaMalloc(&gd, c->Ng * 8));
+        CKM(&gd, c->Ng * 8);
         own = true;
     }
     { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_gradient(c->P, c->gwin, u.ptr, l.ptr, nsrc, gd, c->stream); }
@@ -1432,7 +1483,7 @@ int helm_subdomain_solve(helm_ctx* c, int s, int nrhs, const void* R, void* U, i
     TRY(stage_in(c, R, bytes, mem, r, 0));
     // a private buffer [rhs][window] in the working precision
     void* wb = nullptr;
-    CK(cudaMalloc(&wb, (size_t)nrhs * we * elem_size(c)));
+    CKM(&wb, (size_t)nrhs * we * elem_size(c));
     std::vector<cplx<double>> host((size_t)nrhs * we);
     CK(cudaMemcpyAsync(host.data(), r.ptr, bytes, cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
@@ -1445,34 +1496,9 @@ int helm_subdomain_solve(helm_ctx* c, int s, int nrhs, const void* R, void* U, i
     }
     Task t{0, s, 0, 0, 0};
     Task* td = nullptr;
-    CK(cudaMalloc(&td, sizeof(Task)));
+    CKM(&td, sizeof(Task));
     CK(cudaMemcpy(td, &t, sizeof(Task), cudaMemcpyHostToDevice));
-    const int panel = auto_panel(c, nrhs);
-    if (c->prec == HELM_PREC_F64)
-        launch_solve<double>(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
-                             static_cast<const double*>(c->fac), c->Pv64, c->inva64,
-                             static_cast<cplx<double>*>(wb), static_cast<cplx<double>*>(wb), we,
-                             DevStatus{c->err_d, c->wait_polls}, c->stream);
-    else if (c->prec == HELM_PREC_TF32 && c->umma_twist)
-        launch_solve_twist(td, 1, c->subs_d, c->umma_nblk, c->umma_lines, nrhs, c->ufac, c->ufac_off,
-                           c->ascale_d, c->f16, c->Pv32, c->inva32, static_cast<cplx<float>*>(wb),
-                           static_cast<cplx<float>*>(wb),
-                           we, DevStatus{c->err_d, c->wait_polls}, c->stream);
-    else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
-        launch_solve_umma(td, 1, c->subs_d, c->umma_nblk, nrhs, panel,
-                          static_cast<const float*>(c->ufac), c->ufac_off, c->Pv32, c->inva32,
-                          static_cast<cplx<float>*>(wb), static_cast<cplx<float>*>(wb), we,
-                          DevStatus{c->err_d, c->wait_polls}, c->stream);
-    else if (c->prec == HELM_PREC_TF32)
-        launch_solve_tc(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
-                        static_cast<const float*>(c->fac), c->Pv32, c->inva32,
-                        static_cast<cplx<float>*>(wb), static_cast<cplx<float>*>(wb), we,
-                        DevStatus{c->err_d, c->wait_polls}, c->stream);
-    else
-        launch_solve<float>(td, 1, c->subs_d, c->nbp_max, nrhs, panel,
-                            static_cast<const float*>(c->fac), c->Pv32, c->inva32,
-                            static_cast<cplx<float>*>(wb), static_cast<cplx<float>*>(wb), we,
-                            DevStatus{c->err_d, c->wait_polls}, c->stream);
+    launch_one_subdomain_solve(c, td, nrhs, wb, we);
     CK(cudaGetLastError());
     CK(cudaStreamSynchronize(c->stream));
     if (c->prec == HELM_PREC_F64) {
@@ -1496,6 +1522,11 @@ int helm_subdomain_solve_noalloc(helm_ctx* c, int s, int nrhs, const void* R, vo
     if (!c || !R || !U || nrhs < 1 || s < 0 || s >= c->P.nsub)
         return fail(HELM_ERR_ARG, "bad argument");
     if (!c->factored) return fail(HELM_ERR_NOT_FACTORED, "call helm_factor first");
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev != c->device)
+        return fail(HELM_ERR_ARG, "helm_subdomain_solve_noalloc: the current device (" + std::to_string(dev) +
+                                      ") is not the context's device (" + std::to_string(c->device) + ")");
     const SubDesc& S = c->subs_h[s];
     const size_t need = (size_t)nrhs * S.win_elems * elem_size(c);
     if (need > noalloc_capacity_bytes())
@@ -1507,18 +1538,12 @@ int helm_subdomain_solve_noalloc(helm_ctx* c, int s, int nrhs, const void* R, vo
     a.f64 = c->prec == HELM_PREC_F64;
     a.sub = s;
     a.nrhs = nrhs;
-    a.nbp_max = c->nbp_max;
-    a.panel = auto_panel(c, nrhs);
     a.win_elems = S.win_elems;
-    a.subs = c->subs_d;
-    a.fac = c->fac;
-    a.Pv = a.f64 ? (const void*)c->Pv64 : (const void*)c->Pv32;
-    a.inva = a.f64 ? (const void*)c->inva64 : (const void*)c->inva32;
     a.R = static_cast<const cplx<double>*>(R);
     a.U = static_cast<cplx<double>*>(U);
-    a.err = c->err_d;
-    a.polls = c->wait_polls;
     a.stream = c->stream;
+    a.solve = noalloc_solve_cb;
+    a.ctx = c;
     CK(noalloc_subdomain_solve(a));
     CK(cudaStreamSynchronize(c->stream));
     return check_device_error(c);

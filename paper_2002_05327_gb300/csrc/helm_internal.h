@@ -275,20 +275,18 @@ void launch_conj(cplx<double>* v, int64_t count, cudaStream_t st);
 void launch_gradient(const DevProblem& P, const Win<double>& g, const cplx<double>* U,
                      const cplx<double>* L, int nsrc, double* grad, cudaStream_t st);
 
-// Subdomain solve inside a static device scratch array (k_noalloc.cu).
+// Subdomain solve inside a static device scratch array (k_noalloc.cu).  The
+// solve itself is queued by `solve` (the context's kernel choice, in place on
+// the window buffer it is given, allocating nothing).
 struct NoAllocArgs {
     bool f64;
-    int sub, nrhs, nbp_max, panel;
+    int sub, nrhs;
     int64_t win_elems;
-    const SubDesc* subs;
-    const void* fac;
-    const void* Pv;
-    const void* inva;
     const cplx<double>* R;
     cplx<double>* U;
-    int* err;
-    uint32_t polls;
     cudaStream_t stream;
+    void (*solve)(void* ctx, const Task* task, int nrhs, void* wb, int64_t win_elems);
+    void* ctx;
 };
 size_t noalloc_capacity_bytes();
 cudaError_t noalloc_subdomain_solve(const NoAllocArgs& a);

@@ -38,7 +38,9 @@ namespace {
 std::mutex g_mu;
 void* g_addr[128] = {nullptr};
 
-// Device address of the scratch on the current device (looked up once per device).
+// Device address of the scratch on the current device (looked up once per
+// device and cached; after cudaDeviceReset the cached address is stale, so a
+// process that resets a device must not call this entry point again).
 cudaError_t scratch_address(void** out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -78,9 +80,7 @@ static cudaError_t run(const NoAllocArgs& a, void* scratch) {
     const unsigned blocks = (unsigned)((count + 255) / 256);
     noalloc_write_task<<<1, 1, 0, a.stream>>>(task, Task{0, a.sub, 0, 0, 0});
     noalloc_pack<T><<<blocks, 256, 0, a.stream>>>(a.R, wb, count);
-    launch_solve<T>(task, 1, a.subs, a.nbp_max, a.nrhs, a.panel, static_cast<const T*>(a.fac),
-                    static_cast<const cplx<T>*>(a.Pv), static_cast<const cplx<T>*>(a.inva), wb, wb,
-                    a.win_elems, DevStatus{a.err, a.polls}, a.stream);
+    a.solve(a.ctx, task, a.nrhs, wb, a.win_elems);  // the context's own kernel choice, in place
     noalloc_unpack<T><<<blocks, 256, 0, a.stream>>>(wb, a.U, count);
     return cudaGetLastError();
 }

@@ -1,18 +1,23 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-Tolerances (relative L2 over the whole output):
-  * FP64 path (HELM_PREC_F64): 1e-10.  Both sides solve the same complex128
-    systems; only the elimination order differs (block Gauss-Jordan vs sparse
-    LU), so the gap is rounding amplified by the local condition numbers.
-  * Mixed path (HELM_PREC_MIXED), raw DDM: 1e-3.  complex64 factors carry a
-    unit roundoff of 6e-8; the block recurrence over ~50-200 lines and the
-    explicit inverses amplify it by the local condition numbers (~1e2-1e3 on
-    these PML blocks).
-  * Tensor-core path (HELM_PREC_TF32), raw DDM: 3e-2.  TF32 keeps 10
-    mantissa bits (unit roundoff 4.9e-4) in every block product; the same
-    amplification as above applies.
-  * After FP64 GMRES (the product's answer): 1e-6 against the global direct
-    solve, the bound the method promises after refinement.
+Every comparison is element-wise, right-hand side by right-hand side
+(tests/parity.py): the relative L2 error of each right-hand side and its
+relative max error max|u - ref| / max|ref| must both be within the tolerance,
+so that a wrong value at a few nodes (a transfer strip, a corner, a seam)
+cannot hide under a norm over the whole output.
+
+Tolerances, from the arithmetic and set at 2-4x the worst case measured on
+GB300 over every case below (raw DDM against the oracle's Algorithm 3.1/4.1):
+  * FP64 path (HELM_PREC_F64): 1e-12 (measured <= 1.2e-14).  Both sides solve
+    the same complex128 systems; only the elimination order differs.
+  * complex64 SIMT path (HELM_PREC_MIXED): 1e-5 (measured <= 5.5e-6).
+    complex64 factors carry a unit roundoff of 6e-8, amplified by the block
+    recurrence and the local condition numbers of the PML blocks.
+  * Tensor-core paths (TF32, FP16 with power-of-two scales): 3e-3 (measured
+    <= 7.5e-4).  Both keep 10 mantissa bits (unit roundoff 4.9e-4) in every
+    block product.
+  * After FP64 GMRES (the product's answer): 1e-6 per right-hand side against
+    the global direct solve, the bound the method promises after refinement.
 """
 import dataclasses
 
@@ -20,13 +25,14 @@ import numpy as np
 import pytest
 
 import workloads as W
+from parity import assert_close
 from oracle import adjoint as OA
 from oracle import ddm as OD
 from oracle import helmholtz as OH
 
 pytestmark = pytest.mark.gpu
 
-TOL = {0: 1e-10, 1: 1e-3, 2: 3e-2, 3: 3e-2, 4: 3e-2, 5: 3e-2}
+TOL = {0: 1e-12, 1: 1e-5, 2: 3e-3, 3: 3e-3, 4: 3e-3, 5: 3e-3}
 PRECS = [0, 1, 2, 3, 4, 5]
 
 
@@ -84,6 +90,20 @@ def _nonuniform():
 CASES["2d-nonuniform-3x3"] = _nonuniform
 
 
+def _face():
+    """Sources half a cell inside and one cell past the internal face between
+    boxes 1 and 2 along x: the result is dominated by what crosses that face
+    (the transfer strips and the corner transfers of the neighbouring boxes)."""
+    wl = W.small_2d(nx=60, ny=52, nbx=4, nby=3, nrhs=2)
+    h, c = wl.h, wl.cuts
+    y = 0.5 * (c[1][1] + c[1][2]) * h
+    f = W.gaussian_sources(wl.n, wl.pml, h, [((c[0][2] - 1.5) * h, y), ((c[0][2] + 0.5) * h, y)], h)
+    return dataclasses.replace(wl, f=f)
+
+
+CASES["2d-face-4x3"] = _face
+
+
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("case", sorted(CASES))
 def test_apply_ddm_matches_algorithm(H, case, prec):
@@ -93,7 +113,7 @@ def test_apply_ddm_matches_algorithm(H, case, prec):
     ctx = _ctx(H, wl, prec)
     u = H.helm_apply_ddm(ctx, wl.f)
     ref = OD.ddm_solution(wl)
-    assert rel(u, ref) < TOL[prec], rel(u, ref)
+    assert_close(u, ref, TOL[prec], TOL[prec], (case, prec))
     ctx.close()
 
 
@@ -107,7 +127,7 @@ def test_alternative_3d_sweep_order_matches_algorithm(H, prec):
     u = H.helm_apply_ddm(ctx, wl.f)
     ctx.close()
     ref = OD.ddm_solution(wl, order=1)
-    assert rel(u, ref) < TOL[prec], rel(u, ref)
+    assert_close(u, ref, TOL[prec], TOL[prec], ("order 1", prec))
     if prec == 0:
         assert rel(u, OD.ddm_solution(wl, order=0)) > 1e-6
     with pytest.raises(H.HelmError):
@@ -128,7 +148,8 @@ def test_subdomain_solve_matches_local_direct_solve(H, prec):
         R = rng.standard_normal((3,) + sub.shape) + 1j * rng.standard_normal((3,) + sub.shape)
         u = H.helm_subdomain_solve(ctx, s, R)
         ref = part.local_solve(sub, R)
-        assert rel(u, ref) < {0: 1e-11, 1: 1e-4, 2: 1e-2, 3: 1e-2, 4: 1e-2, 5: 1e-2}[prec], (s, rel(u, ref))
+        tol = {0: 1e-12, 1: 1e-5}.get(prec, 3e-3)  # measured <= 4.4e-15, 2.5e-6, 8.3e-4
+        assert_close(u, ref, tol, tol, (s, prec))
     ctx.close()
 
 
@@ -140,7 +161,7 @@ def test_config1_ddm_fp64(H):
     ctx = _ctx(H, wl, 0)
     u = H.helm_apply_ddm(ctx, wl.f)
     ref = OD.ddm_solution(wl)
-    assert rel(u, ref) < 1e-10
+    assert_close(u, ref, 1e-12, 1e-12, "config 1")
     assert rel(u, OH.solve_global(wl)) < 5e-4
     ctx.close()
 
@@ -151,7 +172,7 @@ def test_gmres_reaches_global_solution(H, prec):
     ctx = _ctx(H, wl, prec)
     x, st = H.helm_solve(ctx, wl.f, rtol=1e-10, maxit=60)
     ref = OH.solve_global(wl)
-    assert rel(x, ref) < 1e-6, rel(x, ref)
+    assert_close(x, ref, 1e-6, 1e-6, ("gmres", prec))
     assert st["resid"] <= 1e-10
     ctx.close()
 
@@ -168,12 +189,12 @@ def test_stationary_iteration_matches_algorithm(H):
     u, st = H.helm_iterate(ctx, wl.f, rtol=1e-30, maxit=3, allow_noconv=True)
     ctx.close()
     assert st["applications"] == 3
-    assert rel(u, us[-1]) < 1e-10, rel(u, us[-1])
+    assert_close(u, us[-1], 1e-12, 1e-12, "u_3")
     assert abs(st["resid"] - res[-1]) <= 1e-3 * res[-1], (st["resid"], res[-1])
     ctx = _ctx(H, wl, 5)
     u, st = H.helm_iterate(ctx, wl.f, rtol=1e-10, maxit=60)
     ctx.close()
-    assert rel(u, OH.solve_global(wl)) < 1e-6
+    assert_close(u, OH.solve_global(wl), 1e-6, 1e-6, "stationary fp16")
     assert st["resid"] <= 1e-10
 
 
@@ -187,7 +208,7 @@ def test_residual_matches_operator(H):
     A, J = OH.global_operator(wl)
     nr = wl.f.shape[0]
     ref = (wl.f.reshape(nr, -1) * J[None] - (A @ u.reshape(nr, -1).T).T).reshape(u.shape)
-    assert rel(r, ref) < 1e-13
+    assert_close(r, ref, 1e-13, 1e-13, "residual")
     ctx.close()
 
 
@@ -209,10 +230,10 @@ def test_adjoint_and_gradient(H):
         return lu.solve(np.ascontiguousarray(b.reshape(b.shape[0], -1).T)).T.reshape(b.shape)
 
     lam_ref = OA.adjoint_solve(solve, g_src)
-    assert rel(lam, lam_ref) < 1e-6
+    assert_close(lam, lam_ref, 1e-6, 1e-6, "adjoint")
     g = H.helm_gradient(ctx, u, lam)
     g_ref = OA.gradient(wl, u, lam)
-    assert rel(g, g_ref) < 1e-12
+    assert_close(g[None], g_ref[None], 1e-12, 1e-12, "gradient")
     ctx.close()
 
 
@@ -229,6 +250,23 @@ def test_errors_are_reported(H):
     with pytest.raises(H.HelmError) as e:
         H.helm_solve(ctx, wl.f, rtol=1e-14, maxit=1)
     assert e.value.code == H.HELM_ERR_NO_CONVERGENCE
+    ctx.close()
+
+
+def test_device_memory_cap_refuses_the_factors(H):
+    """helm_config.max_device_bytes set just above what setup holds: helm_factor
+    is refused with HELM_ERR_OOM before it allocates, the context holds no more
+    than the cap, and it can still be destroyed."""
+    wl = W.small_2d()
+    probe = H.helm_setup_workload(wl, precision=1)
+    setup_bytes = H.helm_device_bytes(probe)
+    probe.close()
+    cap = setup_bytes + 1024
+    ctx = H.helm_setup_workload(wl, precision=1, max_device_bytes=cap)
+    with pytest.raises(H.HelmError) as e:
+        H.helm_factor(ctx)
+    assert e.value.code == H.HELM_ERR_OOM
+    assert H.helm_device_bytes(ctx) <= cap
     ctx.close()
 
 
@@ -258,7 +296,7 @@ def test_expired_wait_is_reported_and_context_stays_usable(H, prec):
     bad.close()
     good = _ctx(H, wl, prec)
     u = H.helm_apply_ddm(good, wl.f)
-    assert rel(u, OD.ddm_solution(wl)) < TOL[prec]
+    assert_close(u, OD.ddm_solution(wl), TOL[prec], TOL[prec], ("after timeout", prec))
     good.close()
 
 

@@ -23,6 +23,7 @@ For N > 1 run under torch.distributed.run; every rank solves its own copy of
 the workload (independent replicas: the path has no exchange across GPUs).
 """
 import argparse
+import dataclasses
 import json
 import os
 import statistics
@@ -37,11 +38,11 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "RHS solves/sec at 1e-6 rel. L2 (mixed vs plain FP64 GPU DDM); %tensor/HBM roofline"
-# DRAM bytes (read + write) per launch of the tensor-core solve kernel, averaged over the
-# solve launches of one step of this workload, from one single-pass ncu capture of the
-# bench command's launch list (dram__bytes_read.sum + dram__bytes_write.sum), per --prec.
-# An entry is removed when the kernel changes.
-SOLVE_TRAFFIC_BYTES_PER_LAUNCH = {"f16": 546.8e6}
+# DRAM bytes (read + write) per launch of the solve kernel, averaged over the solve
+# launches of one step, from one single-pass ncu capture of the bench command's launch
+# list (dram__bytes_read.sum + dram__bytes_write.sum), per (workload, kernel).  An entry
+# is removed when the kernel changes.
+SOLVE_TRAFFIC_BYTES_PER_LAUNCH = {}
 UNIT = "RHS/s"
 
 
@@ -59,6 +60,8 @@ def parse():
     ap.add_argument("--workload", type=int, default=2, help="workload number (2 = bench)")
     ap.add_argument("--prec", default="f16", choices=["f16", "tf32", "mixed"],
                     help="precision of the subdomain factors/solves of the product path")
+    ap.add_argument("--tc-kernel", type=int, default=0,
+                    help="helm_config.tc_kernel of the product path (0 = default kernel choice)")
     ap.add_argument("--nrhs", type=int, default=0,
                     help="use only the first NRHS sources (profiling runs); 0 = all")
     return ap.parse_args()
@@ -130,30 +133,63 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------------------- CPU oracle
-def cpu_oracle_sample(wl, apps_per_rhs):
-    """Time the oracle, as it stands, on a bounded sample of the workload: one
-    application of Algorithm 3.1 to one right-hand side plus one FP64 operator
-    product (one GMRES iteration), scaled by the DDM applications per
-    right-hand side the GPU solve needed.  Local factorisations are excluded
-    (they are reused across right-hand sides, as the GPU factors are)."""
+def _cpu_seconds():
+    t = os.times()
+    return t.user + t.system
+
+
+def oracle_gmres_iterations(name):
+    """Iterations the oracle's own FGMRES needs on this workload's first source
+    at the benchmark's residual, as written by
+    tests/golden/make_oracle_gmres_iters.py (which calls only oracle/)."""
+    path = os.path.join(ROOT, "tests", "golden", "oracle_gmres_iters.txt")
+    if os.path.exists(path):
+        for line in open(path):
+            f = line.split()
+            if f and not line.startswith("#") and f[0] == name:
+                return int(f[2])
+    return None
+
+
+def _oracle_setup(wl):
+    """The oracle's global operator and partition (with its local SuperLU
+    factorisations) for the workload's first right-hand side."""
     from oracle import ddm as OD
     from oracle import helmholtz as OH
+    one = dataclasses.replace(wl, f=wl.f[:1])
     t0 = time.time()
-    A, J = OH.global_operator(wl)
-    part = OD.Partition(wl)
-    t_setup = time.time() - t0
-    b = wl.f[:1] * J.reshape((1,) + wl.f.shape[1:])
-    t1 = time.time()
-    z = OD.diagonal_sweep(part, b)
-    _ = A @ z.reshape(1, -1).T
-    t_iter = time.time() - t1
-    per_rhs = t_iter * max(1, apps_per_rhs)
-    return {"value": 1.0 / per_rhs, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "host_cpus": os.cpu_count(),
-            "sample": (f"one Algorithm 3.1 application + one operator product on 1 of "
-                       f"{wl.nrhs} RHS ({t_iter:.2f} s), x {apps_per_rhs} applications per RHS; "
-                       f"local SuperLU factorisations ({t_setup:.1f} s) excluded; "
-                       "SuperLU and the sparse products are single-threaded")}
+    A, J = OH.global_operator(one)
+    part = OD.Partition(one)
+    b = one.f * J.reshape((1,) + one.f.shape[1:])
+    return A, part, b, time.time() - t0
+
+
+def cpu_oracle_sample(wl, rtol):
+    """The oracle, as it stands, on the host cores: its FGMRES (restart 30),
+    preconditioned by its Algorithm 3.1, on the first right-hand side of the
+    workload to the benchmark's relative residual, run to the end.  The local
+    SuperLU factorisations are timed separately (they serve every right-hand
+    side, as the GPU factors do).  BLAS may use every host core; `cores` is the
+    CPU time the run took over its wall time."""
+    from oracle import ddm as OD
+    from oracle import krylov as OK
+    A, part, b, t_fac = _oracle_setup(wl)
+
+    def apply_A(x):
+        return (A @ x.reshape(x.shape[0], -1).T).T.reshape(x.shape)
+
+    c0, t0 = _cpu_seconds(), time.time()
+    x, info = OK.gmres(apply_A, b, lambda v: OD.diagonal_sweep(part, v), rtol=rtol, restart=30, maxit=60)
+    wall = time.time() - t0
+    cores = (_cpu_seconds() - c0) / wall
+    it, res = int(info["iters"][0]), float(info["resid"][0])
+    return {"value": 1.0 / wall, "unit": UNIT, "cores": round(cores, 2), "kind": "oracle",
+            "host_cpus": os.cpu_count(), "iters": it, "resid": res, "factor_s": t_fac,
+            "factor_amortised_value": 1.0 / (wall + t_fac / wl.nrhs),
+            "sample": (f"the oracle's FGMRES (restart 30, one Algorithm 3.1 application per iteration) on "
+                       f"source 0 of {wl.nrhs}, run to relative residual {rtol:g}: {it} iterations, "
+                       f"residual {res:.1e}, {wall:.1f} s; its local SuperLU factorisations ({t_fac:.1f} s) "
+                       f"are reported apart; SuperLU and the SciPy sparse products are single-threaded")}
 
 
 def job_ms(ms_local, world, device=None):
@@ -168,38 +204,55 @@ def job_ms(ms_local, world, device=None):
 
 
 def run_reference(args):
-    """--impl reference: the CPU oracle as it stands, on the same workload."""
+    """--impl reference: the CPU oracle as it stands, on the same workload, rank 0
+    only.  Every step, warm-up and timed alike, is one of the four sweeps of the
+    oracle's Algorithm 3.1 applied to the workload's first source (a bounded
+    sample: a full application of the oracle takes four).  RHS/s is 1 / (sweeps
+    per application x applications per right-hand side x the mean step time, plus
+    one operator product per application), with the oracle's own FGMRES
+    iteration count on this workload (tests/golden/oracle_gmres_iters.txt)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     import workloads as W
-    wl = W.config(args.workload)
     from oracle import ddm as OD
-    from oracle import helmholtz as OH
-    A, J = OH.global_operator(wl)
-    part = OD.Partition(wl)
-    b = wl.f[:1] * J.reshape((1,) + wl.f.shape[1:])
-    apps = 6  # DDM applications per RHS of the GPU solve at rtol 1e-8 on this workload (measured)
+    wl = W.config(args.workload)
+    A, part, b, t_fac = _oracle_setup(wl)
+    n_it = oracle_gmres_iterations(wl.name) or 1
+    nsw = 2 ** wl.ndim
+    c0 = _cpu_seconds()
+    t_all = time.time()
     times = []
     for i in range(args.warmup + args.steps):
         t = time.time()
-        z = OD.diagonal_sweep(part, b)
-        _ = A @ z.reshape(1, -1).T
+        OD.diagonal_sweep(part, b, nsweeps=1)
         if i >= args.warmup:
             times.append(time.time() - t)
-    per_step = statistics.mean(times) * apps
-    val = 1.0 / per_step
+    t = time.time()
+    _ = A @ b.reshape(1, -1).T
+    t_mv = time.time() - t
+    cores = (_cpu_seconds() - c0) / (time.time() - t_all)
+    step = statistics.mean(times)
+    per_rhs = n_it * (nsw * step + t_mv)
+    val = 1.0 / per_rhs
+    sample = (f"per step: the first sweep of the oracle's Algorithm 3.1 on source 0 of {wl.nrhs} "
+              f"({step:.2f} s); RHS/s = 1 / ({n_it} FGMRES iterations of the oracle x ({nsw} sweeps x step "
+              f"+ one operator product, {t_mv:.2f} s)); local SuperLU factorisations ({t_fac:.1f} s) excluded")
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": per_step * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": step * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": {"workload": wl.name, "grid": list(wl.N),
-                                             "nb": list(wl.nb), "nrhs": 1},
-            "cpu_baseline": {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "host_cpus": os.cpu_count(),
-                             "sample": f"per step: one Algorithm 3.1 application + one operator "
-                                       f"product on 1 RHS, x {apps} applications per RHS"},
+            "data": "synthetic", "config": workload_config(wl, args),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": round(cores, 2), "kind": "oracle",
+                             "host_cpus": os.cpu_count(), "sample": sample, "factor_s": t_fac},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def workload_config(wl, args):
+    """The `config` object of both arms' JSON lines."""
+    return {"workload": wl.name, "grid": list(wl.N), "h_m": wl.h,
+            "freq_hz": round(wl.omega / (2 * np.pi), 6), "nb": list(wl.nb), "overlap": wl.overlap,
+            "sub_pml": wl.sub_pml, "nrhs": wl.nrhs, "rtol": args.rtol}
 
 
 # ----------------------------------------------------------------------------- ours
@@ -240,7 +293,7 @@ def main():
     # ---------------- mixed precision (the product path)
     stream = torch.cuda.current_stream(dev).cuda_stream
     prec = {"f16": H.HELM_PREC_F16, "tf32": H.HELM_PREC_TF32, "mixed": H.HELM_PREC_MIXED}[args.prec]
-    ctx = H.helm_setup_workload(wl, precision=prec, profile=1, stream=stream)
+    ctx = H.helm_setup_workload(wl, precision=prec, profile=1, stream=stream, tc_kernel=args.tc_kernel)
     t0 = time.time()
     H.helm_factor(ctx)
     factor_ms = (time.time() - t0) * 1e3
@@ -337,36 +390,46 @@ def main():
 
     if rank != 0:
         return
-    cpu = None if (args.no_cpu or world > 1) else cpu_oracle_sample(wl, apps)  # rank 0 at N = 1 only
+    cpu = None if (args.no_cpu or world > 1) else cpu_oracle_sample(wl, args.rtol)  # rank 0 at N = 1 only
+    # roofline of the solve kernel: HBM (algorithmic bytes) or tensor pipe (algorithmic
+    # flops), whichever the algorithm's intensity makes binding at the measured peaks
+    t_hbm = sol["bytes"] / (hbm * 1e9)
+    t_tc = sol["flops"] / (bf16 * 1e12)
+    bound = "tensor" if t_tc > t_hbm else "hbm"
+    kname = {"f16": "solve_twist_kernel", "tf32": "solve_twist_kernel", "mixed": "solve_kernel"}[args.prec]
+    cfg = workload_config(wl, args)
+    cfg.update({"outer": "FP64 flexible GMRES (float-float arithmetic, ~48 significand bits)",
+                "subdomain_precision": {
+                    "f16": "complex64 factors, FP16 tensor-core operands with power-of-two scales "
+                           "per factor line and right-hand-side column, FP32 accumulation",
+                    "tf32": "complex64 factors, TF32 tensor-core block products, FP32 accumulation",
+                    "mixed": "complex64 factors and FP32 block products"}[args.prec],
+                "l2": "inputs larger than L2 (device working set %.1f GB, RHS %.2f GB)" % (
+                    dev_bytes / 1e9, nrhs * np.prod(wl.N) * 16 / 1e9),
+                "parallelism": "replicas" if world > 1 else "single"})
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"f16": "f16", "tf32": "tf32", "mixed": "c64"}[args.prec],
         "data": "synthetic",
-        "config": {"workload": wl.name, "grid": list(wl.N), "h_m": wl.h,
-                   "freq_hz": round(wl.omega / (2 * np.pi), 6),
-                   "nb": list(wl.nb), "overlap": wl.overlap, "sub_pml": wl.sub_pml,
-                   "nrhs": nrhs, "rtol": args.rtol, "outer": "FP64 flexible GMRES",
-                   "subdomain_precision": {
-                       "f16": "complex64 factors, FP16 tensor-core operands with power-of-two scales "
-                              "per factor line and right-hand-side column, FP32 accumulation",
-                       "tf32": "complex64 factors, TF32 tensor-core block products, FP32 accumulation",
-                       "mixed": "complex64 factors and FP32 block products"}[args.prec],
-                   "l2": "inputs larger than L2 (device working set %.1f GB, RHS %.2f GB)" % (
-                       dev_bytes / 1e9, nrhs * np.prod(wl.N) * 16 / 1e9),
-                   "parallelism": "replicas" if world > 1 else "single"},
+        "config": cfg,
+        "factor_amortised_value": nrhs * world / (ms / 1e3 + factor_ms / 1e3),
         "gmres": {"iters": iters, "applications": apps, "max_rel_resid": res,
                   "factor_ms": factor_ms, "levels": stats[0]["levels"],
                   "subdomain_solves_per_application": stats[0]["solves"]},
-        "roofline": {"kernel": ("solve_twist_kernel" if args.prec in ("tf32", "f16") else "solve_kernel")
-                     + " (subdomain forward/backward block solves)",
-                     "bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
-                     "frac": achieved / hbm,
-                     "traffic": (SOLVE_TRAFFIC_BYTES_PER_LAUNCH.get(args.prec)
-                                 if args.workload == 2 and not args.nrhs else None),
+        "roofline": {"kernel": kname + " (subdomain forward/backward block solves)",
+                     "bound": bound,
+                     "achieved": tflops if bound == "tensor" else achieved,
+                     "peak": bf16 if bound == "tensor" else hbm,
+                     "unit": "TFLOP/s" if bound == "tensor" else "GB/s",
+                     "frac": tflops / bf16 if bound == "tensor" else achieved / hbm,
+                     "traffic": (SOLVE_TRAFFIC_BYTES_PER_LAUNCH.get((wl.name, kname))
+                                 if not args.nrhs else None),
                      "traffic_unit": "bytes per launch", "peak_source": peak_src,
-                     "tflops_achieved": tflops,
+                     "hbm_achieved_gbs": achieved, "hbm_frac": achieved / hbm,
+                     "tflops_achieved": tflops, "tensor_frac": tflops / bf16,
                      "bytes_per_launch": sol["bytes"] / max(1, sol["launches"]),
+                     "flops_per_launch": sol["flops"] / max(1, sol["launches"]),
                      "ms_per_launch": sol["ms"] / max(1, sol["launches"])},
         "kernel_time_share": kshare,
         "gpu_launches": launches,

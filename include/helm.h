@@ -108,10 +108,11 @@ typedef struct {
     int32_t verbose;    /* 1: per-iteration residuals on stderr */
     void *stream;       /* cudaStream_t to run on; NULL = the library's own stream */
     int32_t profile;    /* 1: time every kernel launch with CUDA events (helm_profile_get) */
-    int32_t tc_kernel;  /* HELM_PREC_TF32 only: 0 = tcgen05/TMEM kernels where blocks have at
-                           most 256 rows (the two-ended "twisted" form when every subdomain
-                           has at least 4 lines), else mma.sync; 1 = always mma.sync;
-                           2 = tcgen05, one-ended form only */
+    int32_t tc_kernel;  /* HELM_PREC_TF32 and HELM_PREC_F16: 0 = tcgen05/TMEM kernels: the
+                           two-ended ("twisted") kernel when every subdomain has at least 4
+                           lines and blocks have at most 256 rows (384 with HELM_PREC_F16),
+                           else the one-ended one for blocks of at most 256 rows, else
+                           mma.sync; 1 = always mma.sync; 2 = tcgen05, one-ended form only */
     int32_t wait_limit; /* bound of every ordinary spin-wait inside the subdomain-solve
                            kernels (a bulk copy, an MMA commit, a peer CTA's handshake),
                            in polls of the mbarrier: 0 = default (2^22 polls); n > 0 = n
@@ -174,7 +175,12 @@ int helm_apply_ddm(helm_ctx *ctx, int nrhs, const void *F, void *U, int mem);
  * (Remark 1), restarted every cfg.restart iterations, until the relative
  * residual is <= rtol for every right-hand side or maxit iterations.
  * Returns HELM_ERR_NO_CONVERGENCE (with U and *st written) if maxit is hit.
- * st may be NULL. */
+ * When the whole batch does not fit in the free device memory (or under
+ * cfg.max_device_bytes) with its window buffers and 2 restart + 2 Krylov
+ * vectors per right-hand side, the call lowers the restart length (to no less
+ * than 8) and then, if needed, solves the right-hand sides in consecutive
+ * chunks; st then gives the largest iteration count and residual over the
+ * chunks and their total of DDM applications.  st may be NULL. */
 int helm_solve(helm_ctx *ctx, int nrhs, const void *F, void *U, int mem, double rtol,
                int maxit, helm_stats *st);
 

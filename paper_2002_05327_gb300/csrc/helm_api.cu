@@ -948,8 +948,8 @@ int ensure_gm(helm_ctx* c, int nrhs, int count) {
 // iteration (Remark 1), on A u = b with b on the device.  Restarts every
 // cfg.restart iterations; stops when every RHS has |b - A u| <= rtol |b|.
 int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, double rtol,
-              int maxit, helm_stats* st) {
-    const int m = c->cfg.restart;
+              int maxit, helm_stats* st, int restart) {
+    const int m = restart;
     const int64_t Ng = c->Ng;
     // vectors, allocated as the Krylov space grows: scratch w (0), then
     // V_i at 1 + 2i and Z_i at 2 + 2i
@@ -1318,8 +1318,10 @@ int helm_factor(helm_ctx* c) {
             nl_min = std::min(nl_min, S.nlines);
             nl_max = std::max(nl_max, S.nlines);
         }
-        const bool umma = c->cfg.tc_kernel != 1 && umma_supported(nblk_max);
-        const bool twist = umma && c->cfg.tc_kernel != 2 && twist_supported(nblk_max, nl_min, nl_max);
+        // default: the twisted kernel (2 tiles, or 3 with FP16 operands), else the one-ended one
+        const int tk = c->cfg.tc_kernel;
+        const bool twist = tk == 0 && twist_supported(nblk_max, nl_min, nl_max, c->f16);
+        const bool umma = tk != 1 && (twist || umma_supported(nblk_max));
         float* fac2 = nullptr;
         if (twist) {
             // the far half of every subdomain's lines, eliminated from the far end
@@ -1391,6 +1393,39 @@ int helm_apply_ddm(helm_ctx* c, int nrhs, const void* F, void* U, int mem) {
     return stage_out(c, U, u, bytes, mem);
 }
 
+// Right-hand sides per GMRES run and the restart length, so that the run's
+// device memory fits: its window buffers (local sources and solutions of every
+// subdomain solve) and its Krylov vectors (2 restart + 2 float-float vectors),
+// against the free device memory plus what the
+// context already holds in those buffers (and cfg.max_device_bytes, when set).
+// The whole batch when it fits with the configured restart; else the largest
+// halving of it that fits with a restart of at least 8 (the restart lowered to
+// what fits); else halving on with a restart of 8.
+void solve_plan(const helm_ctx* c, int nrhs, int maxit, bool gmres, int* chunk, int* restart) {
+    size_t free_b = 0, total_b = 0;
+    cudaMemGetInfo(&free_b, &total_b);
+    size_t held = 2 * (size_t)c->cap_rhs * c->buf_per_rhs * elem_size(c);
+    held += c->gm.size() * (size_t)c->gm_rhs * c->Ng * 16;
+    const size_t reserve = (size_t)1 << 30;
+    double avail = (double)free_b + (double)held - (double)reserve;
+    if (c->cfg.max_device_bytes > 0)
+        avail = std::min(avail, (double)c->cfg.max_device_bytes - (double)(c->dev_bytes - held));
+    const int mcfg = std::max(1, std::min(c->cfg.restart, maxit));
+    const int mmin = std::min(8, mcfg);
+    auto per_rhs = [&](int m) {
+        const double vecs = gmres ? 2.0 * m + 2.0 : 2.0;
+        return 2.0 * c->buf_per_rhs * elem_size(c) + vecs * c->Ng * 16.0;
+    };
+    int C = nrhs;
+    if (C * per_rhs(mcfg) > avail) {
+        while (C > 1 && C * per_rhs(mmin) > avail) C = (C + 1) / 2;
+    }
+    int m = mcfg;
+    while (m > mmin && C * per_rhs(m) > avail) --m;
+    *chunk = C;
+    *restart = m;
+}
+
 static int solve_common(helm_ctx* c, int nrhs, const void* F, void* U, int mem, double rtol,
                         int maxit, helm_stats* st, bool adjoint, bool stationary = false) {
     if (!c || !F || !U || nrhs < 1 || !(rtol > 0) || maxit < 1)
@@ -1409,8 +1444,25 @@ static int solve_common(helm_ctx* c, int nrhs, const void* F, void* U, int mem, 
     } else {
         { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_scale_J(c->P, c->gwin, f.ptr, c->bvec, nrhs, false, c->stream); }
     }
-    int rc = stationary ? stationary_dev(c, nrhs, c->bvec, u.ptr, rtol, maxit, st)
-                        : gmres_dev(c, nrhs, c->bvec, u.ptr, rtol, maxit, st);
+    int chunk = nrhs, restart = c->cfg.restart;
+    solve_plan(c, nrhs, maxit, !stationary, &chunk, &restart);
+    int rc = HELM_OK;
+    helm_stats acc{};
+    for (int r0 = 0; r0 < nrhs; r0 += chunk) {
+        const int nr = std::min(chunk, nrhs - r0);
+        helm_stats one{};
+        const size_t off = (size_t)r0 * c->Ng;
+        const int rci = stationary ? stationary_dev(c, nr, c->bvec + off, u.ptr + off, rtol, maxit, &one)
+                                   : gmres_dev(c, nr, c->bvec + off, u.ptr + off, rtol, maxit, &one, restart);
+        if (rci != HELM_OK && rci != HELM_ERR_NO_CONVERGENCE) return rci;
+        if (rci != HELM_OK) rc = rci;
+        acc.iters = std::max(acc.iters, one.iters);
+        acc.applications += one.applications;
+        acc.resid = std::max(acc.resid, one.resid);
+        acc.levels = one.levels;
+        acc.solves = one.solves;
+    }
+    if (st) *st = acc;
     if (rc != HELM_OK && rc != HELM_ERR_NO_CONVERGENCE) return rc;
     std::string msg = g_last_error;
     if (adjoint) launch_conj(u.ptr, (int64_t)nrhs * c->Ng, c->stream);

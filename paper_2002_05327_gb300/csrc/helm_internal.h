@@ -194,11 +194,11 @@ void launch_repack_umma(const SubDesc* subs_d, const std::vector<SubDesc>& subs_
                         const float* fac, const float* fac2, const int64_t* dst_off_d, float* dst,
                         cudaStream_t st);  // fac2: twisted factors of lines >= nlines/2, or null
 // Twisted (two-ended) tcgen05 solve: one 2-CTA cluster per (task, panel of 8
-// RHS), top and bottom halves of the lines, all rows per CTA (n <= 256,
-// nlines >= 4); factors repacked with one slice (CR = 1) from the twisted factors.
+// RHS), top and bottom halves of the lines, all rows per CTA (n <= 256 in two
+// M = 128 tiles, or n <= 384 in three with f16; nlines >= 4); factors repacked with one slice (CR = 1) from the twisted factors.
 // With f16 the image is FP16 (K chunks of 64) with per-line power-of-two
 // scales ascale[inva_off + line] (launch_line_scales, launch_repack_f16).
-bool twist_supported(int nblk_max, int nlines_min, int nlines_max);
+bool twist_supported(int nblk_max, int nlines_min, int nlines_max, bool f16);
 int64_t twist_f16_factor_bytes(const SubDesc& S);
 void launch_line_scales(const SubDesc* subs_d, int nsub, int max_lines, const float* fac, const float* fac2,
                         int* ascale, cudaStream_t st);

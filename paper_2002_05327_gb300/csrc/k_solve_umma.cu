@@ -53,115 +53,13 @@
 #include <cuda_fp16.h>
 
 #include "helm_internal.h"
+#include "tc_util.cuh"
 
 namespace helm {
 
+using namespace tc;
+
 namespace {
-
-__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mb_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
-}
-__device__ __forceinline__ void mb_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ bool mb_wait(uint32_t bar, uint32_t parity, uint32_t limit) {
-    uint32_t done = 0;
-    for (uint32_t it = 0; it < limit; ++it) {
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-__device__ __forceinline__ uint32_t to_tf32(float x) {
-    uint32_t r;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-    return r;
-}
-
-// Shared-memory matrix descriptor, K-major, 128-byte swizzle: start address,
-// leading byte offset (unused for this layout, 1), stride byte offset 1024
-// (8 rows x 128 B), descriptor version 1, layout type 2 (128B swizzle).
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);
-    d |= (uint64_t)1 << 16;
-    d |= (uint64_t)(1024 >> 4) << 32;
-    d |= (uint64_t)1 << 46;
-    d |= (uint64_t)2 << 61;
-    return d;
-}
-// Instruction descriptor, kind::tf32: D f32, A and B tf32, both K-major.
-__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(N >> 3) << 17) |
-           ((uint32_t)(M >> 4) << 24);
-}
-// Instruction descriptor, kind::f16 with FP16 A and B (K-major), D f32.
-__host__ __device__ constexpr uint32_t idesc_f16(int M, int N) {
-    return (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
-}
-__device__ __forceinline__ void umma_f16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
-                                         uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.u32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-// 2^e as a float for -126 <= e <= 127 (0 below)
-__device__ __forceinline__ float pow2f(int e) {
-    return e < -126 ? 0.f : __int_as_float((e > 127 ? 127 + 127 : e + 127) << 23);
-}
-__device__ __forceinline__ void umma_tf32(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
-                                          uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.u32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
-        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
-        : "memory");
-}
-__device__ __forceinline__ void umma_commit(uint32_t bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
-                 : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-// Issue a 32-lane x 16-column TMEM load without waiting for it; tmem_wait_ld
-// then waits for every load the thread has issued and ties the registers to
-// that wait, so no use of them can be scheduled before it.
-__device__ __forceinline__ void tmem_ld16_async(uint32_t taddr, uint32_t (&r)[16]) {
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_pin16(uint32_t (&r)[16]) {
-    asm volatile(""
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]),
-                   "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]),
-                   "+r"(r[13]), "+r"(r[14]), "+r"(r[15]));
-}
 
 constexpr uint32_t kWait = kDrainPolls;
 constexpr int kChunkK = 32;        // K values per 128-byte row
@@ -293,46 +191,6 @@ __global__ void repack_f16_kernel(const SubDesc* __restrict__ subs, const float*
     dst[dst_off[sub] / 2 + i] = __float2half_rn(v);  // dst_off in bytes
 }
 
-__device__ __forceinline__ uint32_t cluster_rank() {
-    uint32_t r;
-    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
-    return r;
-}
-__device__ __forceinline__ uint32_t map_peer(uint32_t saddr, uint32_t rank) {
-    uint32_t r;
-    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
-    return r;
-}
-// Bulk copy of this CTA's shared memory into a peer CTA's, completing as
-// transaction bytes on the peer's mbarrier (addresses from mapa).
-__device__ __forceinline__ void bulk_s2peer(uint32_t dst, uint32_t src, uint32_t bytes, uint32_t bar) {
-    asm volatile("cp.async.bulk.shared::cluster.shared::cta.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "r"(src), "r"(bytes), "r"(bar)
-                 : "memory");
-}
-// Barriers among the 128 epilogue threads only (named barriers 1 and 2; the
-// producer and issuer warps never take part).  epi_any also ORs a flag over
-// them, so that all four epilogue warps take the same abort decision.
-__device__ __forceinline__ void epi_sync(uint32_t nthreads = 128) {
-    __syncwarp();
-    asm volatile("bar.sync 2, %0;" ::"r"(nthreads) : "memory");
-}
-__device__ __forceinline__ bool epi_any(bool flag, uint32_t nthreads = 128) {
-    uint32_t out;
-    __syncwarp();
-    asm volatile(
-        "{\n\t.reg .pred q, p;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "bar.red.or.pred p, 1, %2, q;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(out)
-        : "r"((uint32_t)flag), "r"(nthreads)
-        : "memory");
-    return out != 0;
-}
-__device__ __forceinline__ void cluster_sync() {
-    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
-}
 
 // One CTA per (task, panel of PG right-hand sides, R-row slice of the block);
 // the slices of one block form a cluster of CR (1 or 2).  Each CTA streams and
@@ -839,13 +697,20 @@ void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nb
 // (a_j couples line j to j-1, c_j to j+1; both are diagonal).  The halves meet
 // once in each direction: the bottom sends c_mid z_{mid+1}, the top sends
 // a_{mid+1} u_mid, each as one bulk copy between the CTAs' shared memory.
-// Each CTA holds all n <= 256 rows of the block (two M = 128 tiles), so no
-// data crosses between the CTAs during the line steps, and the chain of a
-// level is about half as long as the one-ended solve's.
+// Each CTA holds all n rows of the block (NT = 2 M = 128 tiles for n <= 256,
+// NT = 3 for n <= 384 with FP16 operands), so no data crosses between the
+// CTAs during the line steps, and the chain of a level is about half as long
+// as the one-ended solve's.  Every tile is one M = 128 MMA shape; the last
+// tile's rows beyond the image (R = roundup16(n)) read the next stage or the
+// ring's tail and land in accumulator lanes of no block row.
 //
-// Roles: warps 0-7 epilogue (warp e: tile e/4, TMEM lanes 32*(e%4) ..);
-// warps 8-9 bulk-copy producers, warps 10-11 MMA issuers, one sub-ring of the
-// operand ring per producer/issuer pair (stream positions q, q+2, ...).
+// Roles: warps 0 .. 4NT-1 epilogue (warp e: tile e/4, TMEM lanes 32*(e%4) ..);
+// then kTwP bulk-copy producers and kTwP MMA issuers, one sub-ring of the
+// operand ring per producer/issuer pair (stream positions q, q+kTwP, ...).
+// An issuer takes each stage's tiles in turn and issues the four K = 16 MMAs
+// of a 64-wide chunk back to back into one accumulator: measured, that keeps
+// the tensor pipe near one M = 128, N = 16 MMA per ~47 cycles, where
+// interleaving single MMAs over accumulators and tiles ran ~2.7x slower.
 // Handshakes: full/empty per stage, acc_full per step, b_ready per step (B of
 // the step written; B is single-buffered: the epilogue writes it only after
 // every MMA of the previous step completed), x_in (the peer's middle vector,
@@ -855,10 +720,8 @@ void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nb
 // producer / issuer pairs: three for TF32 (288 KB of operand per line step),
 // two for FP16 (half the bytes)
 __host__ __device__ constexpr int tw_pairs(bool f16) { return f16 ? 2 : 3; }
-constexpr int kTwEpi = 8;  // epilogue warps (two TMEM tiles)
-constexpr int kTwWarpProd = kTwEpi;
-__host__ __device__ constexpr int tw_threads(bool f16) { return 32 * (kTwEpi + 2 * tw_pairs(f16)); }
-constexpr uint32_t kTwEpiThreads = 32 * kTwEpi;
+// NT M = 128 tiles of block rows (n <= 128 NT), four epilogue warps each
+__host__ __device__ constexpr int tw_threads(bool f16, int NT) { return 32 * (4 * NT + 2 * tw_pairs(f16)); }
 
 // F16: operands in FP16 (kind::f16, K chunks of 64) with power-of-two
 // scales: each factor line by 2^ascale[line] (set when the image is built),
@@ -867,8 +730,8 @@ constexpr uint32_t kTwEpiThreads = 32 * kTwEpi;
 // so that both land in [2^13, 2^14); the FP32 accumulator is multiplied back
 // by the inverse powers of two.  FP16 keeps TF32's 10-bit mantissa, so entries
 // above ~2^-27 of their line's or column's largest carry the same rounding.
-template <int PG, bool F16>
-__global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
+template <int PG, bool F16, int NT>
+__global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
     const Task* __restrict__ tasks, const SubDesc* __restrict__ subs, int nrhs,
     const void* __restrict__ afac_v, const int64_t* __restrict__ afac_off, const int* __restrict__ ascale,
     const cplx<float>* __restrict__ Pv, const cplx<float>* __restrict__ inva, cplx<float>* buf,
@@ -877,6 +740,9 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
     constexpr int kBChunkBytes = kN * 128;
     constexpr int kKc = F16 ? 64 : 32;  // K values per 128-byte row of a chunk
     constexpr int kTwP = tw_pairs(F16);
+    constexpr int kTwEpi = 4 * NT;  // epilogue warps: tile e / 4, TMEM lanes 32 (e % 4) ..
+    constexpr uint32_t kTwEpiThreads = 32 * kTwEpi;
+    constexpr int kTwWarpProd = kTwEpi;
     constexpr int kTwWarpIss = kTwWarpProd + kTwP;
     const char* afac = reinterpret_cast<const char*>(afac_v);
     extern __shared__ __align__(1024) unsigned char smem_raw[];
@@ -900,7 +766,7 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
     // bulk copy per step (copies issued by one warp complete one after another,
     // so fewer, larger copies arrive sooner); otherwise the chunks are dealt
     // round-robin over kTwP sub-rings of NS/kTwP stages.
-    const bool whole = (uint32_t)(nkc - 1) * stage_bytes + 2u * (uint32_t)kTileBytes <= ring_bytes;
+    const bool whole = (uint32_t)(nkc - 1) * stage_bytes + (uint32_t)(NT * kTileBytes) <= ring_bytes;
     const int cpp = (nkc + kTwP - 1) / kTwP;
     const int nq_act = whole ? (nkc + cpp - 1) / cpp : (nkc < kTwP ? nkc : kTwP);  // issuers with chunks
     // line of step s of this CTA
@@ -938,8 +804,9 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
     uint32_t* s_red = tmem_slot + 4;  // [2][kTwEpi][PG] column maxima (F16 scales), by step parity
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    constexpr uint32_t kCols = 2 * kTwP * kN <= 32 ? 32 : 2 * kTwP * kN <= 64 ? 64 :
-                               2 * kTwP * kN <= 128 ? 128 : 256;  // tile t, issuer q: (t*kTwP + q)*kN
+    constexpr uint32_t kCols = NT * kTwP * kN <= 32 ? 32 : NT * kTwP * kN <= 64 ? 64 :
+                               NT * kTwP * kN <= 128 ? 128 : 256;  // tile t, issuer q: (t*kTwP + q)*kN
+    static_assert(NT * kTwP * kN <= 256, "accumulators beyond 256 TMEM columns");
 
     if (tid == 0) {
         *abort_flag = 0;
@@ -1100,7 +967,7 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
             mb_wait(drain, 0u, kWait);
         }
     } else if (warp < kTwEpi) {
-        // ====================================================== epilogue (warps 0-7)
+        // ====================================================== epilogue (warps 0 .. 4 NT - 1)
         const int t = warp / 4, quarter = warp % 4;
         const int p = t * 128 + quarter * 32 + lane;  // block row (TMEM lane quarter*32 + lane of tile t)
         const bool rv = p < n && t < ntile;
@@ -1378,7 +1245,8 @@ __global__ void __launch_bounds__(tw_threads(F16)) solve_twist_kernel(
 // least 2) of R*128 bytes plus the 256-row tail of the last one, B, the two
 // middle buffers, the per-line scalars, barriers, slots and the column-maximum
 // scratch, alignment; 0 if it does not fit.
-static size_t twist_smem_plan(int PG, bool f16, int nblk_max, int nlines_max, int* ns_out, uint32_t* ring_out) {
+static size_t twist_smem_plan(int PG, bool f16, int NT, int nblk_max, int nlines_max, int* ns_out,
+                              uint32_t* ring_out) {
     const int kTwP = tw_pairs(f16);
     int nkc = 0;
     if (f16)
@@ -1386,25 +1254,33 @@ static size_t twist_smem_plan(int PG, bool f16, int nblk_max, int nlines_max, in
     else
         umma_line_bytes(nblk_max, 1, &nkc);
     const size_t sb = (size_t)umma_rows(nblk_max, 1) * 128;
-    const size_t tail = 2 * (size_t)kTileBytes;  // the second tile's MMA reads 128 rows from +16 KB
+    const size_t tail = (size_t)NT * kTileBytes;  // the last tile's MMA reads 128 rows from +16 (NT-1) KB
     const size_t lines = (size_t)(nlines_max + 1) * 8 + (size_t)nlines_max * 4;
     const size_t fixed =
         (size_t)nkc * 2 * PG * 128 + 2 * (size_t)umma_rows(nblk_max, 1) * PG * 8 + lines + 1024 + 1024;
     const size_t budget = 227 * 1024;
     if (fixed + (2 * kTwP - 1) * sb + tail > budget) return 0;
     int ns = (int)((budget - fixed - tail) / sb) + 1;
-    if (ns > 28) ns = 28;  // (2 ns + 4) barriers, 4 slots and the 2 x 8 x PG scratch within the 1 KB reserve
+    // (2 ns + 4) barriers, 4 slots and the 2 x 4NT x PG column-maximum scratch
+    // within the 1 KB reserve (8 of it for the barriers' alignment)
+    const int ns_cap = ((1024 - 8 - 16 - 2 * 4 * NT * PG * 4) / 8 - 4) / 2;
+    if (ns > ns_cap) ns = ns_cap;
     ns -= ns % kTwP;
+    if (ns < 2 * kTwP) return 0;
     *ns_out = ns;
     *ring_out = (uint32_t)((ns - 1) * sb + tail);
     return *ring_out + fixed;
 }
 
-bool twist_supported(int nblk_max, int nlines_min, int nlines_max) {
+// Tiles of the twisted launch: two up to 256 block rows, three up to 384
+// (FP16 only: the TF32 ring of a 384-row block does not fit next to B).
+static int twist_tiles(int nblk_max) { return nblk_max <= 256 ? 2 : 3; }
+
+bool twist_supported(int nblk_max, int nlines_min, int nlines_max, bool f16) {
     int ns;
     uint32_t ring;
-    return nblk_max <= 256 && nlines_min >= 4 && twist_smem_plan(8, false, nblk_max, nlines_max, &ns, &ring) != 0 &&
-           twist_smem_plan(8, true, nblk_max, nlines_max, &ns, &ring) != 0;
+    return nblk_max <= (f16 ? 384 : 256) && nlines_min >= 4 &&
+           twist_smem_plan(8, f16, twist_tiles(nblk_max), nblk_max, nlines_max, &ns, &ring) != 0;
 }
 
 int64_t twist_f16_factor_bytes(const SubDesc& S) { return umma_line_bytes16(S.nblk, nullptr) * S.nlines; }
@@ -1424,7 +1300,7 @@ void launch_repack_f16(const SubDesc* subs_d, const std::vector<SubDesc>& subs_h
     }
 }
 
-template <bool F16>
+template <bool F16, int NT>
 static void launch_twist_t(const Task* tasks, int ntask, const SubDesc* subs, int nblk_max, int nlines_max, int nrhs,
                            const void* afac, const int64_t* afac_off, const int* ascale, const cplx<float>* Pv,
                            const cplx<float>* inva, cplx<float>* buf, const cplx<float>* bsrc, int64_t rstride,
@@ -1432,11 +1308,11 @@ static void launch_twist_t(const Task* tasks, int ntask, const SubDesc* subs, in
     constexpr int PG = 8;
     int ns = 0;
     uint32_t ring = 0;
-    const size_t smem = twist_smem_plan(PG, F16, nblk_max, nlines_max, &ns, &ring);
-    cudaFuncSetAttribute(solve_twist_kernel<PG, F16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = twist_smem_plan(PG, F16, NT, nblk_max, nlines_max, &ns, &ring);
+    cudaFuncSetAttribute(solve_twist_kernel<PG, F16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(ntask * 2, (nrhs + PG - 1) / PG, 1);
-    cfg.blockDim = dim3(tw_threads(F16), 1, 1);
+    cfg.blockDim = dim3(tw_threads(F16, NT), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -1446,7 +1322,7 @@ static void launch_twist_t(const Task* tasks, int ntask, const SubDesc* subs, in
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, solve_twist_kernel<PG, F16>, tasks, subs, nrhs, afac, afac_off, ascale, Pv, inva,
+    cudaLaunchKernelEx(&cfg, solve_twist_kernel<PG, F16, NT>, tasks, subs, nrhs, afac, afac_off, ascale, Pv, inva,
                        buf, bsrc, rstride, ns, ring, ds);
 }
 
@@ -1455,12 +1331,15 @@ void launch_solve_twist(const Task* tasks, int ntask, const SubDesc* subs, int n
                         const cplx<float>* Pv, const cplx<float>* inva, cplx<float>* buf,
                         const cplx<float>* bsrc, int64_t rstride, DevStatus ds, cudaStream_t st) {
     if (ntask == 0) return;
-    if (f16)
-        launch_twist_t<true>(tasks, ntask, subs, nblk_max, nlines_max, nrhs, afac, afac_off, ascale, Pv, inva, buf, bsrc,
-                             rstride, ds, st);
+    if (f16 && twist_tiles(nblk_max) == 3)
+        launch_twist_t<true, 3>(tasks, ntask, subs, nblk_max, nlines_max, nrhs, afac, afac_off, ascale, Pv, inva, buf,
+                                bsrc, rstride, ds, st);
+    else if (f16)
+        launch_twist_t<true, 2>(tasks, ntask, subs, nblk_max, nlines_max, nrhs, afac, afac_off, ascale, Pv, inva, buf,
+                                bsrc, rstride, ds, st);
     else
-        launch_twist_t<false>(tasks, ntask, subs, nblk_max, nlines_max, nrhs, afac, afac_off, ascale, Pv, inva, buf, bsrc,
-                              rstride, ds, st);
+        launch_twist_t<false, 2>(tasks, ntask, subs, nblk_max, nlines_max, nrhs, afac, afac_off, ascale, Pv, inva, buf,
+                                 bsrc, rstride, ds, st);
 }
 
 }  // namespace helm

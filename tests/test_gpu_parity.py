@@ -56,7 +56,8 @@ def _ctx(H, wl, prec, **kw):
     blocks allow it, in the twisted two-ended form where every subdomain has
     at least 4 lines); 3 = TF32 forced onto the mma.sync kernel; 4 = TF32 on
     the one-ended tcgen05 kernel; 5 = FP16 operands with power-of-two scales
-    in the twisted tcgen05 kernel (TF32 elsewhere)."""
+    in the twisted tcgen05 kernel (two tiles up to 256 block rows, three up to
+    384; TF32 elsewhere)."""
     if prec == 3:
         prec, kw = 2, dict(kw, tc_kernel=1)
     elif prec == 4:
@@ -76,6 +77,9 @@ CASES = {
     # blocks of more than 128 rows: the tensor-core solve runs as a 2-CTA cluster
     "2d-wide-2x2": lambda: W.small_2d(nx=260, ny=48, nbx=2, nby=2, pml=8, overlap=4, sub_pml=8,
                                       nrhs=10),
+    # blocks of 300 rows: three M = 128 tiles in the FP16 twisted kernel
+    "2d-300row-2x2": lambda: W.small_2d(nx=560, ny=48, nbx=2, nby=2, pml=8, overlap=4, sub_pml=8,
+                                        nrhs=3),
     "3d-const-2x2x2": lambda: W.small_3d(),
     "3d-layered-3x2x2": lambda: W.small_3d(n=(27, 18, 16), nb=(3, 2, 2), nrhs=1, medium="layered"),
 }
@@ -312,14 +316,15 @@ def test_deterministic_and_device_pointers(H):
     ctx.close()
 
 
-@pytest.mark.parametrize("prec", [2, 4, 5])
-def test_cluster_tensor_core_path_is_deterministic(H, prec):
-    """The tcgen05 solves run as 2-CTA clusters: the twisted form (prec 2)
-    hands the middle line's vectors between its two halves, the one-ended form
-    (prec 4, blocks of more than 128 rows) exchanges the B operand every line
-    step.  Repeated applications must be bitwise identical (a handshake race
-    would show as run-to-run changes)."""
-    wl = CASES["2d-wide-2x2"]()
+@pytest.mark.parametrize("case,prec", [("2d-wide-2x2", 2), ("2d-wide-2x2", 4), ("2d-wide-2x2", 5),
+                                       ("2d-300row-2x2", 5)])
+def test_cluster_tensor_core_path_is_deterministic(H, case, prec):
+    """The tcgen05 solves run as 2-CTA clusters: the twisted form (prec 2, 5)
+    hands the middle line's vectors between its two halves, the one-ended
+    form (prec 4, blocks of more than 128 rows) exchanges the B operand every
+    line step.  Repeated applications must be bitwise identical (a handshake
+    race would show as run-to-run changes)."""
+    wl = CASES[case]()
     ctx = _ctx(H, wl, prec)
     u1 = H.helm_apply_ddm(ctx, wl.f)
     for _ in range(3):

@@ -1,13 +1,15 @@
 """Parity at the full sizes of the seismic-shaped workloads.
 
-The 1064^2 layered workload (8x8 subdomains, 64 point sources) runs in the
-launch configuration the benchmark times: all right-hand sides in one call,
-FP16 tensor-core subdomain solves (power-of-two scaled operands, FP32
-accumulation), FP64 GMRES to a relative residual of 1e-8, on the caller's
-stream.  The oracle checks, one by one, the outputs it can
-afford:
-  * sampled right-hand sides against its global direct solve (1e-6 relative
-    L2, the accuracy the method promises after refinement);
+The 2088x1576 nonuniform workload (12x9 subdomains, windows up to 280 block
+rows, 256 point sources) and the 1064^2 layered workload (8x8 subdomains, 64
+point sources) run in the launch configuration the benchmark times: all
+right-hand sides in one call, FP16 tensor-core subdomain solves (power-of-two
+scaled operands, FP32 accumulation), FP64 GMRES to a relative residual of
+1e-8, on the caller's stream.  The oracle checks, one by one and element by
+element (tests/parity.py: relative L2 and relative max error per right-hand
+side), the outputs it can afford:
+  * sampled right-hand sides against its global direct solve (1e-6, the
+    accuracy the method promises after refinement);
   * one right-hand side of the raw DDM (both precisions) against its own
     Algorithm 3.1;
 and every right-hand side through a property that holds at any size: the true
@@ -26,6 +28,7 @@ import pytest
 import scipy.sparse.linalg as spla
 
 import workloads as W
+from parity import assert_close
 from oracle import adjoint as OA
 from oracle import ddm as OD
 from oracle import helmholtz as OH
@@ -34,6 +37,7 @@ pytestmark = pytest.mark.gpu
 
 SAMPLE = [0, 37, 63]   # right-hand sides checked against the direct solve
 DDM_RHS = 5            # right-hand side checked against the oracle's Algorithm 3.1
+SAMPLE4 = [0, 101, 255]  # of the 2088x1576 workload's 256
 
 
 @pytest.fixture(scope="module")
@@ -79,8 +83,7 @@ def gpu2(H, wl2):
 def test_bench_workload_sampled_rhs_match_direct_solve(wl2, gpu2):
     U, _, st = gpu2
     ref = OH.solve_global(dataclasses.replace(wl2, f=wl2.f[SAMPLE]))
-    errs = [rel(U[s], ref[i]) for i, s in enumerate(SAMPLE)]
-    assert max(errs) <= 1e-6, (errs, st)
+    assert_close(U[SAMPLE], ref, 1e-6, 1e-6, ("1064^2 GMRES vs direct", st))
 
 
 def test_bench_workload_every_rhs_true_residual(wl2, gpu2):
@@ -97,10 +100,14 @@ def test_bench_workload_every_rhs_true_residual(wl2, gpu2):
 
 def test_bench_workload_raw_f16_ddm_matches_algorithm(gpu2, oracle_ddm2):
     """One DDM application of all 64 right-hand sides in one call; the sampled
-    one equals the oracle's Algorithm 3.1 within the tolerance of the 10-bit
-    mantissa that FP16 shares with TF32."""
+    one equals the oracle's Algorithm 3.1 within the rounding of the 10-bit
+    mantissa that FP16 shares with TF32.  At this size (42 dependency levels,
+    blocks of ~180 rows, 1064 lines per sweep direction) the measured error is
+    4.0e-3 relative L2 on GB300, above the small cases' 7.5e-4: the rounding of
+    each block product accumulates over more line steps and more transfers.
+    Tolerance 1e-2."""
     _, z, _ = gpu2
-    assert rel(z, oracle_ddm2) < 3e-2
+    assert_close(z[None], oracle_ddm2[None], 1e-2, 1e-2, "1064^2 raw FP16 DDM")
 
 
 def test_bench_workload_raw_fp64_ddm_matches_algorithm(H, wl2, oracle_ddm2):
@@ -113,7 +120,7 @@ def test_bench_workload_raw_fp64_ddm_matches_algorithm(H, wl2, oracle_ddm2):
     Z = H.helm_apply_ddm(ctx, torch.from_numpy(wl2.f).cuda())
     z = Z[DDM_RHS].cpu().numpy()
     ctx.close()
-    assert rel(z, oracle_ddm2) < 1e-10
+    assert_close(z[None], oracle_ddm2[None], 1e-12, 1e-12, "1064^2 raw FP64 DDM")
 
 
 # ----------------------------------------------------------------------------- adjoint
@@ -187,23 +194,28 @@ def test_adjoint_gradient_full_size(H):
 
 
 # ----------------------------------------------------------------------------- nonuniform
-def test_nonuniform_workload_full_size_true_residual(H):
+def test_nonuniform_workload_full_size(H):
     """The 2088x1576 nonuniform workload (12x9 subdomains with widths 96..224;
-    windows up to 280 rows, on the mma.sync tensor-core kernel) with a sample of
-    16 of its 256 point sources: GMRES with the FP16 mode (TF32 on this kernel)
-    to a relative residual of 1e-8, checked for every right-hand side with the
-    oracle's FP64 operator."""
+    windows up to 280 block rows, on the three-tile twisted tcgen05 kernel)
+    with all 256 point sources in one call, as the benchmark runs it (the call
+    may split the batch into chunks to fit the device): GMRES with the FP16
+    mode to a relative residual of 1e-8.  Three sampled right-hand sides match
+    the oracle's global direct solve element by element within 1e-6, and every
+    right-hand side's true residual, with the oracle's FP64 operator, is within
+    1.5e-8."""
     import torch
-    wl = W.config(4, src=list(range(0, 256, 16)))
+    wl = W.config(4)
     ctx = H.helm_setup_workload(wl, precision=H.HELM_PREC_F16,
                                 stream=torch.cuda.current_stream().cuda_stream)
     H.helm_factor(ctx)
     U, st = H.helm_solve(ctx, torch.from_numpy(wl.f).cuda(), rtol=1e-8, maxit=60)
-    U = U.cpu().numpy()
     ctx.close()
+    U = U.cpu().numpy()
     A, J = OH.global_operator(wl)
     res = []
     for s in range(wl.nrhs):
         b = J * wl.f[s].ravel()
         res.append(np.linalg.norm(b - A @ U[s].ravel()) / np.linalg.norm(b))
     assert max(res) <= 1.5e-8, (max(res), st)
+    ref = OH.solve_global(dataclasses.replace(wl, f=wl.f[SAMPLE4]))
+    assert_close(U[SAMPLE4], ref, 1e-6, 1e-6, ("2088x1576 GMRES vs direct", st))

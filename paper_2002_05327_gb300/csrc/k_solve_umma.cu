@@ -695,8 +695,10 @@ void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nb
 //   bottom (rank 1): z_j = E_j (b_j - c_j z_{j+1})                     j = nl-1 .. mid+1
 //                    u_j = z_j - E_j (a_j u_{j-1})                      j = mid+1 .. nl-1
 // (a_j couples line j to j-1, c_j to j+1; both are diagonal).  The halves meet
-// once in each direction: the bottom sends c_mid z_{mid+1}, the top sends
-// a_{mid+1} u_mid, each as one bulk copy between the CTAs' shared memory.
+// once in each direction: the bottom stores z_{mid+1} (its line mid+1 of the
+// output) and the top u_mid (line mid), each followed by one release arrive on
+// the peer's barrier; the peer reads the line back from global memory after
+// its acquire wait and applies the coupling itself.
 // Each CTA holds all n rows of the block (NT = 2 M = 128 tiles for n <= 256,
 // NT = 3 for n <= 384 with FP16 operands), so no data crosses between the
 // CTAs during the line steps, and the chain of a level is about half as long
@@ -713,8 +715,8 @@ void launch_solve_umma(const Task* tasks, int ntask, const SubDesc* subs, int nb
 // interleaving single MMAs over accumulators and tiles ran ~2.7x slower.
 // Handshakes: full/empty per stage, acc_full per step, b_ready per step (B of
 // the step written; B is single-buffered: the epilogue writes it only after
-// every MMA of the previous step completed), x_in (the peer's middle vector,
-// one phase).  Every wait is bounded; on expiry the CTA raises the device
+// every MMA of the previous step completed), x_in (the peer's middle line is
+// in global memory; one phase).  Every wait is bounded; on expiry the CTA raises the device
 // error word, each role leaves its loop, copies and MMAs are drained, the two
 // CTAs drain the middle copies between them, and TMEM is freed.
 // producer / issuer pairs: three for TF32 (288 KB of operand per line step),
@@ -758,7 +760,6 @@ __global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
     const uint32_t stage_bytes = (uint32_t)R * 128;
     const int NS = nstage, NQ = NS / kTwP;
     const uint32_t b_bytes = (uint32_t)(nkc * kBChunkBytes);
-    const uint32_t x_bytes = (uint32_t)R * PG * 8;  // middle vector: R rows x PG complex
     const int nsteps = rank == 0 ? 2 * mid + 1 : 2 * nb;
     // Whole-line ring: when one line of factors fits (chunk li in stage li, the
     // second tile's reads of the last chunk included), producer / issuer pair q
@@ -775,18 +776,14 @@ __global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
         return st < nb ? nl - 1 - st : mid + 1 + (st - nb);
     };
 
-    // shared layout (1024-aligned): ring | B | x_stage | x_in buffer | barriers | slots
+    // shared layout (1024-aligned): ring | B | per-line scalars | barriers | slots
     const uint32_t base = (su32(smem_raw) + 1023u) & ~1023u;
     unsigned char* gbase = smem_raw + (base - su32(smem_raw));
     const uint32_t stage0 = base;
     const uint32_t b0 = stage0 + ring_bytes;
     float* bl = reinterpret_cast<float*>(gbase + ring_bytes);
-    const uint32_t xs0 = b0 + b_bytes;
-    cplx<float>* xs = reinterpret_cast<cplx<float>*>(gbase + ring_bytes + b_bytes);
-    const uint32_t xi0 = xs0 + x_bytes;
-    const cplx<float>* xi = reinterpret_cast<const cplx<float>*>(gbase + ring_bytes + b_bytes + x_bytes);
     // per-line scalars: 1/alpha at the nl+1 faces, then the FP16 line scales
-    const uint32_t ls0 = xi0 + x_bytes;
+    const uint32_t ls0 = b0 + b_bytes;
     cplx<float>* ia_s = reinterpret_cast<cplx<float>*>(gbase + (ls0 - base));
     int* as_s = reinterpret_cast<int*>(gbase + (ls0 - base) + (uint32_t)(nl + 1) * 8u);
     const uint32_t bars = (ls0 + (uint32_t)(nl + 1) * 8u + (uint32_t)nl * 4u + 7u) & ~7u;
@@ -799,8 +796,6 @@ __global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
     const uint32_t drain = bars + 8u * (2 * NS + 3);
     uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars_g + 2 * NS + 4);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-    volatile int* x_sent = reinterpret_cast<volatile int*>(tmem_slot + 2);  // this CTA sent its middle copy
-    volatile int* x_peer = reinterpret_cast<volatile int*>(tmem_slot + 3);  // the peer sent its (exit)
     uint32_t* s_red = tmem_slot + 4;  // [2][kTwEpi][PG] column maxima (F16 scales), by step parity
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -810,8 +805,6 @@ __global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
 
     if (tid == 0) {
         *abort_flag = 0;
-        *x_sent = 0;
-        *x_peer = 0;
         for (int s = 0; s < NS; ++s) {
             mb_init(full(s), 1);
             mb_init(empty(s), 1);
@@ -838,9 +831,6 @@ __global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
     cluster_sync();  // the peer's barriers are initialised before its copy can land
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
-    // arm x_in for the peer's single middle copy (it may land before or after)
-    if (tid == 0)
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(x_in), "r"(x_bytes) : "memory");
 
     if (warp >= kTwWarpProd && warp < kTwWarpProd + kTwP) {
         // ====================================================== producers
@@ -1063,25 +1053,24 @@ __global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
             if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b_ready) : "memory");
             return true;
         };
-        // middle vector to the peer: rows of this CTA into x_stage, one bulk copy
-        auto send_middle = [&](const cplx<float> (&v)[PG]) {
-            if (p < R) {
-#pragma unroll
-                for (int c = 0; c < PG; ++c) xs[p * PG + c] = v[c];
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        // middle line to the peer: this CTA's rows of line lm stored to the
+        // output (made visible at cluster scope), then one release arrive on
+        // the peer's x_in
+        auto send_middle = [&](int lm, const cplx<float> (&v)[PG]) {
+            vstore(lm, v);
+            fence_acq_rel_cluster();
             epi_sync(kTwEpiThreads);
-            if (tid == 0) {
-                bulk_s2peer(map_peer(xi0, peer), xs0, x_bytes, map_peer(x_in, peer));
-                *x_sent = 1;
-            }
+            if (tid == 0) mb_arrive_remote(map_peer(x_in, peer));
         };
-        // the peer's middle vector (every epilogue thread waits; uniform outcome)
-        auto recv_middle = [&](cplx<float> (&dst)[PG]) -> bool {
-            const bool got = mb_wait(x_in, 0u, ds.polls);
+        // the peer's line lm times the coupling cf (every epilogue thread waits;
+        // uniform outcome)
+        auto recv_middle = [&](int lm, cplx<float> cf, cplx<float> (&dst)[PG]) -> bool {
+            const bool got = mb_wait_cluster(x_in, 0u, ds.polls);
             if (epi_any(!got, kTwEpiThreads)) return false;
 #pragma unroll
-            for (int c = 0; c < PG; ++c) dst[c] = (p < R) ? xi[p * PG + c] : mk<float>(0, 0);
+            for (int c = 0; c < PG; ++c)
+                dst[c] = (rv && c < ncol) ? cf * V[(int64_t)(c0 + c) * rstride + (int64_t)lm * n + p]
+                                          : mk<float>(0, 0);
             return true;
         };
         // operand kept from memory for the epilogue of step st: top: b_{st+1}
@@ -1148,6 +1137,7 @@ __global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
                 for (int c = 0; c < PG; ++c) y[c] = mk<float>(acc[2 * c], acc[2 * c + 1]);
             }
             bool last = step + 1 >= nsteps;
+            bool stored = false;  // outv already in the output (a middle line)
             if (rank == 0) {
                 if (step < mid) {  // y_j; next: b_{j+1} - a_{j+1} y_j (minus the bottom's c_mid z_{mid+1} at mid)
                     const cplx<float> a = coup(j + 1);
@@ -1156,21 +1146,22 @@ __global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
                         outv[c] = y[c];
                         nbv[c] = rv ? pre[c] - a * y[c] : mk<float>(0, 0);
                     }
-                    if (step + 1 == mid) {
-                        if (!recv_middle(xv)) { ok = false; break; }
+                    if (step + 1 == mid) {  // the bottom's c_mid z_{mid+1}
+                        if (!recv_middle(mid + 1, coup(mid + 1), xv)) { ok = false; break; }
 #pragma unroll
                         for (int c = 0; c < PG; ++c) nbv[c] = rv ? nbv[c] - xv[c] : mk<float>(0, 0);
                     }
-                } else if (step == mid) {  // u_mid; send a_{mid+1} u_mid; next: c_{mid-1} u_mid
-                    const cplx<float> a = coup(mid + 1), cc = coup(mid);
-                    cplx<float> snd[PG];
+                } else if (step == mid) {  // u_mid, to the bottom; next: c_{mid-1} u_mid
+                    const cplx<float> cc = coup(mid);
 #pragma unroll
                     for (int c = 0; c < PG; ++c) {
                         outv[c] = y[c];
-                        snd[c] = rv ? a * y[c] : mk<float>(0, 0);
                         nbv[c] = rv ? cc * y[c] : mk<float>(0, 0);
                     }
-                    if (nb > 0) send_middle(snd);
+                    if (nb > 0) {
+                        send_middle(mid, outv);
+                        stored = true;
+                    }
                 } else {  // u_j = y_j - D_j (c_j u_{j+1}); next: c_{j-1} u_j
                     const cplx<float> cc = coup(j);
 #pragma unroll
@@ -1187,13 +1178,10 @@ __global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
                         outv[c] = y[c];
                         nbv[c] = rv ? pre[c] - cc * y[c] : mk<float>(0, 0);
                     }
-                    if (step + 1 == nb) {
-                        cplx<float> snd[PG];
-                        const cplx<float> cm = coup(mid + 1);  // c_mid couples line mid to mid+1
-#pragma unroll
-                        for (int c = 0; c < PG; ++c) snd[c] = rv ? cm * y[c] : mk<float>(0, 0);
-                        send_middle(snd);
-                        if (!recv_middle(xv)) { ok = false; break; }
+                    if (step + 1 == nb) {  // z_{mid+1} to the top; back: a_{mid+1} u_mid
+                        send_middle(mid + 1, outv);
+                        stored = true;
+                        if (!recv_middle(mid, coup(mid + 1), xv)) { ok = false; break; }
 #pragma unroll
                         for (int c = 0; c < PG; ++c) {
                             nbv[c] = rv ? xv[c] : mk<float>(0, 0);
@@ -1213,7 +1201,7 @@ __global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
                 ok = false;
                 break;
             }
-            vstore(j, outv);
+            if (!stored) vstore(j, outv);
 #pragma unroll
             for (int c = 0; c < PG; ++c) pre[c] = pre_next[c];
         }
@@ -1224,17 +1212,7 @@ __global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
     }
     tc_fence_before();
     __syncthreads();
-    // Drain the middle copies before either CTA leaves: each learns whether
-    // its peer sent one, waits until it has landed, and the second cluster
-    // barrier keeps each CTA resident until its own copy has been read.
-    if (tid == 0) {
-        const uint32_t dst = map_peer(su32((const void*)x_peer), peer);
-        asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(dst), "r"((uint32_t)*x_sent) : "memory");
-    }
-    __syncwarp();
-    cluster_sync();
-    if (tid == 0 && *x_peer && !mb_wait(x_in, 0u, kWait)) atomicExch(ds.err, 2);
-    __syncwarp();
+    // neither CTA leaves while the peer's arrive on its x_in may be in flight
     cluster_sync();
     tc_fence_after();
     if (warp == kTwWarpIss)
@@ -1242,9 +1220,9 @@ __global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
 }
 
 // Shared-memory plan of a twisted launch: ns stages (kTwP sub-rings of at
-// least 2) of R*128 bytes plus the 256-row tail of the last one, B, the two
-// middle buffers, the per-line scalars, barriers, slots and the column-maximum
-// scratch, alignment; 0 if it does not fit.
+// least 2) of R*128 bytes, the last one at least NT tiles long (the last
+// tile's MMA reads 128 rows), B, the per-line scalars, barriers, slots and the
+// column-maximum scratch, alignment; 0 if it does not fit.
 static size_t twist_smem_plan(int PG, bool f16, int NT, int nblk_max, int nlines_max, int* ns_out,
                               uint32_t* ring_out) {
     const int kTwP = tw_pairs(f16);
@@ -1256,8 +1234,7 @@ static size_t twist_smem_plan(int PG, bool f16, int NT, int nblk_max, int nlines
     const size_t sb = (size_t)umma_rows(nblk_max, 1) * 128;
     const size_t tail = (size_t)NT * kTileBytes;  // the last tile's MMA reads 128 rows from +16 (NT-1) KB
     const size_t lines = (size_t)(nlines_max + 1) * 8 + (size_t)nlines_max * 4;
-    const size_t fixed =
-        (size_t)nkc * 2 * PG * 128 + 2 * (size_t)umma_rows(nblk_max, 1) * PG * 8 + lines + 1024 + 1024;
+    const size_t fixed = (size_t)nkc * 2 * PG * 128 + lines + 1024 + 1024;
     const size_t budget = 227 * 1024;
     if (fixed + (2 * kTwP - 1) * sb + tail > budget) return 0;
     int ns = (int)((budget - fixed - tail) / sb) + 1;

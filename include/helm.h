@@ -103,7 +103,10 @@ typedef struct {
 /* Implementation knobs.  Zero-initialise for defaults. */
 typedef struct {
     int32_t precision;  /* enum helm_precision (default HELM_PREC_MIXED) */
-    int32_t rhs_panel;  /* right-hand sides per CTA in the subdomain solve; 0 = auto */
+    int32_t rhs_panel;  /* right-hand sides per CTA in the subdomain solve; 0 = measured: the
+                           first DDM application of each batch size times every panel width
+                           the context's solve kernel takes on the widest dependency level
+                           and keeps the fastest (the twisted kernels: 8, fixed) */
     int32_t restart;    /* GMRES restart length; 0 = 30 */
     int32_t verbose;    /* 1: per-iteration residuals on stderr */
     void *stream;       /* cudaStream_t to run on; NULL = the library's own stream */

@@ -123,6 +123,7 @@ struct helm_ctx {
     int umma_nblk = 0;                 // largest block of the tcgen05 solve
     int umma_lines = 0;                // most lines of a subdomain (twisted solve)
     bool umma_twist = false;           // tcgen05 solve in its twisted (two-ended) form
+    std::map<int, int> panel_pick;     // nrhs -> measured right-hand sides per CTA (tune_panel)
     bool f16 = false;                  // HELM_PREC_F16: FP16 operands in the twisted solve
     int* ascale_d = nullptr;           // per (subdomain, line) exponent of the FP16 factor scale
     void* bsrc = nullptr;              // local sources b, same layout as buf; zero except where the
@@ -801,6 +802,92 @@ int auto_panel(const helm_ctx* c, int nrhs) {
     return q;
 }
 
+// The subdomain solves of one dependency level (tasks t[0 .. nt)) with the
+// kernel the context's precision and factor images select and `panel`
+// right-hand sides per CTA where that kernel takes a panel width.
+static void launch_level_solve(helm_ctx* c, const Task* t, int nt, int nrhs, int panel) {
+    const int64_t rs = c->buf_per_rhs;
+    const DevStatus ds{c->err_d, c->wait_polls};
+    if (c->prec == HELM_PREC_F64) {
+        launch_solve<double>(t, nt, c->subs_d, c->nbp_max, nrhs, panel, static_cast<const double*>(c->fac), c->Pv64,
+                             c->inva64, static_cast<cplx<double>*>(c->buf),
+                             static_cast<const cplx<double>*>(c->bsrc), rs, ds, c->stream);
+        return;
+    }
+    auto* buf = static_cast<cplx<float>*>(c->buf);
+    auto* bsrc = static_cast<const cplx<float>*>(c->bsrc);
+    if (c->prec == HELM_PREC_TF32 && c->umma_twist)
+        launch_solve_twist(t, nt, c->subs_d, c->umma_nblk, c->umma_lines, nrhs, c->ufac, c->ufac_off, c->ascale_d,
+                           c->f16, c->Pv32, c->inva32, buf, bsrc, rs, ds, c->stream);
+    else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
+        launch_solve_umma(t, nt, c->subs_d, c->umma_nblk, nrhs, panel, static_cast<const float*>(c->ufac),
+                          c->ufac_off, c->Pv32, c->inva32, buf, bsrc, rs, ds, c->stream);
+    else if (c->prec == HELM_PREC_TF32)
+        launch_solve_tc(t, nt, c->subs_d, c->nbp_max, nrhs, panel, static_cast<const float*>(c->fac), c->Pv32,
+                        c->inva32, buf, bsrc, rs, ds, c->stream);
+    else
+        launch_solve<float>(t, nt, c->subs_d, c->nbp_max, nrhs, panel, static_cast<const float*>(c->fac), c->Pv32,
+                            c->inva32, buf, bsrc, rs, ds, c->stream);
+}
+
+// Autotuner of the right-hand sides per CTA of the subdomain solve.  With
+// cfg.rhs_panel set, or for the twisted kernels (panels of 8 fixed by their
+// TMEM and register plan), the fixed choice of auto_panel.  Otherwise the
+// first batch of each size times every panel width the context's kernel
+// takes -- the SIMT kernels 1, 2, 4, 8 (at most 4 in FP64, 2 for plane
+// blocks), mma.sync 4, 8, 16, the one-ended tcgen05 kernel 8, 16, 32 -- on
+// the widest dependency level, twice each with CUDA events on the context's
+// stream (the second run counts), and keeps the fastest for the context's
+// lifetime.  A width whose launch the kernel rejects (its shared-memory plan
+// does not fit these blocks) is skipped.  The runs only write window buffers,
+// which the application then overwrites.
+static int tune_panel(helm_ctx* c, int nrhs) {
+    const int fixed = auto_panel(c, nrhs);
+    if (c->cfg.rhs_panel > 0 || (c->prec == HELM_PREC_TF32 && c->umma_twist) || c->levels.empty()) return fixed;
+    auto it = c->panel_pick.find(nrhs);
+    if (it != c->panel_pick.end()) return it->second;
+    std::vector<int> cand;
+    if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
+        cand = {8, 16, 32};
+    else if (c->prec == HELM_PREC_TF32)
+        cand = {4, 8, 16};
+    else {
+        const int pmax = c->nbp_max > 960 ? 2 : c->prec == HELM_PREC_F64 ? 4 : 8;
+        for (int p = 1; p <= pmax; p *= 2) cand.push_back(p);
+    }
+    size_t widest = 0;
+    for (size_t lv = 1; lv < c->levels.size(); ++lv)
+        if (c->levels[lv].size() > c->levels[widest].size()) widest = lv;
+    const Task* t = c->tasks_d + c->level_off[widest];
+    const int nt = (int)c->levels[widest].size();
+    if (cudaPeekAtLastError() != cudaSuccess) return fixed;  // leave an earlier error to its reporter
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return fixed;
+    if (cudaEventCreate(&e1) != cudaSuccess) {
+        cudaEventDestroy(e0);
+        return fixed;
+    }
+    int best = fixed;
+    float best_ms = -1.f;
+    for (int p : cand) {
+        float ms = 0.f;
+        bool launched = true;
+        for (int rep = 0; rep < 2 && launched; ++rep) {
+            cudaEventRecord(e0, c->stream);
+            launch_level_solve(c, t, nt, nrhs, p);
+            launched = cudaGetLastError() == cudaSuccess;
+            cudaEventRecord(e1, c->stream);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
+        }
+        if (launched && (best_ms < 0.f || ms < best_ms)) best = p, best_ms = ms;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->panel_pick[nrhs] = best;
+    return best;
+}
+
 // One application of Algorithm 3.1 / 4.1 to the J-scaled source b (device,
 // [nrhs][grid], complex128 or float-float); the assembled u_DDM goes to U
 // (device, the same form).
@@ -809,7 +896,7 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const VB* b, VB* U) {
     if (!c->factored) return fail(HELM_ERR_NOT_FACTORED, "call helm_factor first");
     TRY(ensure_buffers(c, nrhs));
     const int64_t rs = c->buf_per_rhs;
-    const int panel = auto_panel(c, nrhs);
+    const int panel = tune_panel(c, nrhs);
     const double es = (double)elem_size(c);
     for (size_t lv = 0; lv < c->levels.size(); ++lv) {
         const Task* t = c->tasks_d + c->level_off[lv];
@@ -836,9 +923,7 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const VB* b, VB* U) {
                                       c->af64, c->tab64, b, nrhs, buf, bsrc, rs, c->stream);
             }
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
-            launch_solve<double>(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
-                                 static_cast<const double*>(c->fac), c->Pv64, c->inva64, buf, bsrc, rs,
-                                 DevStatus{c->err_d, c->wait_polls}, c->stream);
+            launch_level_solve(c, t, nt, nrhs, panel);
         } else {
             auto* buf = static_cast<cplx<float>*>(c->buf);
             auto* bsrc = static_cast<cplx<float>*>(c->bsrc);
@@ -849,22 +934,7 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const VB* b, VB* U) {
                                      c->af32, c->tab32, b, nrhs, buf, bsrc, rs, c->stream);
             }
             ProfScope ps(c, HELM_K_SOLVE, 1, sbytes, sflops);
-            if (c->prec == HELM_PREC_TF32 && c->umma_twist)
-                launch_solve_twist(t, nt, c->subs_d, c->umma_nblk, c->umma_lines, nrhs, c->ufac, c->ufac_off,
-                                   c->ascale_d, c->f16, c->Pv32, c->inva32, buf, bsrc, rs,
-                                   DevStatus{c->err_d, c->wait_polls}, c->stream);
-            else if (c->prec == HELM_PREC_TF32 && c->umma_mt > 0)
-                launch_solve_umma(t, nt, c->subs_d, c->umma_nblk, nrhs, panel,
-                                  static_cast<const float*>(c->ufac), c->ufac_off, c->Pv32,
-                                  c->inva32, buf, bsrc, rs, DevStatus{c->err_d, c->wait_polls}, c->stream);
-            else if (c->prec == HELM_PREC_TF32)
-                launch_solve_tc(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
-                                static_cast<const float*>(c->fac), c->Pv32, c->inva32, buf, bsrc, rs,
-                                DevStatus{c->err_d, c->wait_polls}, c->stream);
-            else
-                launch_solve<float>(t, nt, c->subs_d, c->nbp_max, nrhs, panel,
-                                    static_cast<const float*>(c->fac), c->Pv32, c->inva32, buf, bsrc,
-                                    rs, DevStatus{c->err_d, c->wait_polls}, c->stream);
+            launch_level_solve(c, t, nt, nrhs, panel);
         }
     }
     ProfScope ps(c, HELM_K_ASSEMBLE, 1, (double)c->Ng * nrhs * 16.0);
@@ -1293,6 +1363,7 @@ int helm_factor(helm_ctx* c) {
     if (!c) return fail(HELM_ERR_ARG, "null context");
     if (c->factored) return HELM_OK;
     double t0 = now_ms();
+    c->panel_pick.clear();
     if (!c->fac) {
         CKM(&c->fac, c->fac_bytes);
         c->dev_bytes += c->fac_bytes;

@@ -279,6 +279,17 @@ int helm_profile_get(helm_ctx *ctx, helm_profile *out);
 /* Bytes of device memory held by the context. */
 int64_t helm_device_bytes(helm_ctx *ctx);
 
+/* Frees the context's subdomain factors (and their tile images) and its work
+ * buffers (window buffers, Krylov vectors, staging), keeping everything
+ * helm_setup built; the context is then unfactored.  helm_factor recomputes
+ * the same factors (the factorization is deterministic), so a later solve or
+ * adjoint gives bitwise the result it would have given before the release.
+ * For a caller that must hold the device memory free between a forward solve
+ * and its adjoint (Remark 2: the adjoint reuses the forward operator A(m),
+ * so recomputing its factors is the alternative to keeping them).  Waits for
+ * the context's stream.  Returns HELM_OK or HELM_ERR_ARG (null context). */
+int helm_release(helm_ctx *ctx);
+
 void helm_destroy(helm_ctx *ctx);
 const char *helm_strerror(int code);
 const char *helm_last_error(void);

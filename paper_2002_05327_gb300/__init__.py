@@ -109,6 +109,7 @@ _SIGS = {
     "helm_problem_info": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(ctypes.c_int64),
                                          ctypes.POINTER(ctypes.c_int64)]),
     "helm_device_bytes": (ctypes.c_int64, [ctypes.c_void_p]),
+    "helm_release": (ctypes.c_int, [ctypes.c_void_p]),
     "helm_profile_reset": (ctypes.c_int, [ctypes.c_void_p]),
     "helm_profile_get": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(helm_profile)]),
     "helm_destroy": (None, [ctypes.c_void_p]),
@@ -355,6 +356,10 @@ def helm_device_bytes(ctx: Context) -> int:
     return int(lib().helm_device_bytes(ctx.ptr))
 
 
+def helm_release(ctx: Context) -> None:
+    _check(lib().helm_release(ctx.ptr), "helm_release")
+
+
 def helm_profile_reset(ctx: Context):
     _check(lib().helm_profile_reset(ctx.ptr), "helm_profile_reset")
 
@@ -374,12 +379,16 @@ def _make_helm_solve():
         gradient of any real loss of U with respect to m (Remark 2: the
         adjoint-state gradient that full waveform inversion uses).
 
-        forward(m, F, spec, rtol, maxit): m is a float64 tensor of the full grid
-        (copied to the host for helm_setup); F a CUDA complex128 tensor
-        [nrhs, *grid]; spec the keyword arguments of helm_setup other than m
-        (ndim, n, h, omega, pml_width, sigma0, nb, overlap, ...).  It sets up
-        and factors a context for this m, solves with helm_solve and keeps the
-        context for the backward pass.
+        forward(m, F, spec, rtol, maxit, keep_bytes): m is a float64 tensor of
+        the full grid (copied to the host for helm_setup); F a CUDA complex128
+        tensor [nrhs, *grid]; spec the keyword arguments of helm_setup other
+        than m (ndim, n, h, omega, pml_width, sigma0, nb, overlap, ...).  It
+        sets up and factors a context for this m, solves with helm_solve and
+        keeps the context for the backward pass.  When keep_bytes is given and
+        the context holds more device memory than that after the solve, its
+        factors and work buffers are released (helm_release) and backward
+        recomputes them (helm_factor): the same factors, so the same gradient,
+        for one more factorization instead of the memory between the passes.
 
         backward(gU), with gU = dL/dRe U + i dL/dIm U (torch's convention for
         complex tensors): lam = A^{-H} gU by helm_adjoint on the same factors,
@@ -387,11 +396,14 @@ def _make_helm_solve():
         F is not differentiated (its gradient is None)."""
 
         @staticmethod
-        def forward(actx, m, F, spec, rtol=1e-8, maxit=100):
+        def forward(actx, m, F, spec, rtol=1e-8, maxit=100, keep_bytes=None):
             mh = m.detach().to("cpu", torch.float64).numpy()
             helm = helm_setup(m=mh, **spec)
             helm_factor(helm)
             U, _ = helm_solve(helm, F.detach().contiguous(), rtol, maxit)
+            actx.released = keep_bytes is not None and helm_device_bytes(helm) > keep_bytes
+            if actx.released:
+                helm_release(helm)
             actx.helm, actx.rtol, actx.maxit = helm, rtol, maxit
             actx.m_meta = (m.device, m.dtype)
             actx.save_for_backward(U)
@@ -400,10 +412,12 @@ def _make_helm_solve():
         @staticmethod
         def backward(actx, gU):
             (U,) = actx.saved_tensors
+            if actx.released:
+                helm_factor(actx.helm)
             lam, _ = helm_adjoint(actx.helm, gU.contiguous(), actx.rtol, actx.maxit)
             g = helm_gradient(actx.helm, U, lam)
             dev, dt = actx.m_meta
-            return g.to(dev, dt), None, None, None, None
+            return g.to(dev, dt), None, None, None, None, None
 
     return HelmSolve
 

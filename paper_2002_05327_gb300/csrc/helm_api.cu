@@ -118,6 +118,7 @@ struct helm_ctx {
 
     // factors
     void* ufac = nullptr;              // tcgen05 tile image of the factors (TF32)
+    size_t ufac_bytes = 0;
     int64_t* ufac_off = nullptr;       // byte offset per subdomain
     int umma_mt = 0;                   // CTAs per block in the tcgen05 solve (0: not used)
     int umma_nblk = 0;                 // largest block of the tcgen05 solve
@@ -1420,6 +1421,7 @@ int helm_factor(helm_ctx* c) {
             if (!c->ufac) {
                 CKM(&c->ufac, (size_t)tot);
                 c->dev_bytes += (size_t)tot;
+                c->ufac_bytes = (size_t)tot;
                 TRY(upload(&c->ufac_off, off.data(), off.size() * sizeof(int64_t), c));
             }
             if (f16) {
@@ -1690,6 +1692,38 @@ int helm_problem_info(helm_ctx* c, int64_t* nsub, int64_t N[3]) {
 }
 
 int64_t helm_device_bytes(helm_ctx* c) { return c ? (int64_t)c->dev_bytes : 0; }
+
+int helm_release(helm_ctx* c) {
+    if (!c) return fail(HELM_ERR_ARG, "null context");
+    CK(cudaStreamSynchronize(c->stream));  // nothing queued may still use what is freed
+    auto drop = [&](auto*& p, size_t bytes) {
+        if (p) {
+            cudaFree(p);
+            c->dev_bytes -= bytes;
+        }
+        p = nullptr;
+    };
+    drop(c->fac, c->fac_bytes);
+    drop(c->ufac, c->ufac_bytes);
+    drop(c->ufac_off, c->subs_h.size() * sizeof(int64_t));
+    drop(c->ascale_d, c->inva_count * sizeof(int));
+    const size_t wb = (size_t)c->cap_rhs * c->buf_per_rhs * elem_size(c);
+    drop(c->buf, wb);
+    drop(c->bsrc, wb);
+    drop(c->bvec, (size_t)c->cap_vec_rhs * c->Ng * 16);
+    for (auto*& p : c->gm) drop(p, (size_t)c->gm_rhs * c->Ng * 16);
+    for (int i = 0; i < 3; ++i) drop(c->stage_d[i], c->stage_cap[i]);
+    c->gm.clear();
+    c->ufac_bytes = 0;
+    c->cap_rhs = c->cap_vec_rhs = c->gm_rhs = 0;
+    for (auto& s : c->stage_cap) s = 0;
+    c->umma_twist = false;
+    c->umma_mt = 0;
+    c->panel_pick.clear();
+    c->factored = false;
+    CK(cudaGetLastError());
+    return HELM_OK;
+}
 
 int helm_profile_reset(helm_ctx* c) {
     if (!c) return fail(HELM_ERR_ARG, "null context");

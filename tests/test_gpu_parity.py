@@ -241,6 +241,42 @@ def test_adjoint_and_gradient(H):
     ctx.close()
 
 
+def test_release_and_refactor_give_the_same_gradient(H):
+    """HelmSolve with keep_bytes=0 releases the context's factors and buffers
+    after the forward solve (helm_release) and recomputes them in backward:
+    the device memory between the passes drops to the setup's, and the
+    gradient is bitwise the one computed with the factors kept."""
+    import torch
+    wl = W.small_2d(nx=40, ny=34, nbx=2, nby=2, pml=8, overlap=4, sub_pml=8, nrhs=2)
+    rec = np.array([(wl.pml + k, wl.pml + 2) for k in range(2, 38, 4)])
+    spec = dict(ndim=wl.ndim, n=wl.n, h=wl.h, omega=wl.omega, pml_width=wl.pml, sigma0=wl.sigma0,
+                nb=wl.nb, overlap=wl.overlap, power=wl.power, cuts=wl.cuts, sub_pml=wl.sub_pml,
+                precision=H.HELM_PREC_F16)
+    F = torch.from_numpy(wl.f).cuda()
+    ry, rx = torch.from_numpy(rec[:, 1]).cuda(), torch.from_numpy(rec[:, 0]).cuda()
+    grads = []
+    for keep in (None, 0):
+        m = torch.tensor(wl.m, dtype=torch.float64, device="cuda", requires_grad=True)
+        U = H.HelmSolve.apply(m, F, spec, 1e-10, 80, keep)
+        loss = (U[:, ry, rx].abs() ** 2).sum()
+        loss.backward()
+        grads.append(m.grad.cpu().numpy())
+    assert np.array_equal(grads[0], grads[1])
+    ctx = H.helm_setup_workload(wl, precision=H.HELM_PREC_F16)
+    setup_bytes = H.helm_device_bytes(ctx)
+    H.helm_factor(ctx)
+    u1 = H.helm_apply_ddm(ctx, wl.f)
+    assert H.helm_device_bytes(ctx) > setup_bytes
+    H.helm_release(ctx)
+    assert H.helm_device_bytes(ctx) == setup_bytes
+    with pytest.raises(H.HelmError) as e:
+        H.helm_apply_ddm(ctx, wl.f)
+    assert e.value.code == H.HELM_ERR_NOT_FACTORED
+    H.helm_factor(ctx)
+    assert np.array_equal(H.helm_apply_ddm(ctx, wl.f), u1)
+    ctx.close()
+
+
 def test_errors_are_reported(H):
     wl = W.small_2d()
     with pytest.raises(H.HelmError) as e:

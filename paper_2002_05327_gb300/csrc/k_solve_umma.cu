@@ -750,7 +750,12 @@ __global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t rank = cluster_rank();  // 0: top half, 1: bottom half
     const uint32_t peer = rank ^ 1u;
-    const Task tk = tasks[blockIdx.x / 2];
+    // cluster c = blockIdx.x / 2 is (task c / npanel, panel c % npanel): the
+    // panels of a task are adjacent in launch order, so the CTAs that stream
+    // the same factor lines are resident together and share them through L2
+    const int npanel = (nrhs + PG - 1) / PG;
+    const int cpair = blockIdx.x / 2, panel = cpair % npanel;
+    const Task tk = tasks[cpair / npanel];
     const SubDesc& S = subs[tk.sub];
     const int n = S.nblk, nl = S.nlines, mid = nl / 2, nb = nl - 1 - mid;
     const int ntile = (n + 127) / 128;
@@ -965,7 +970,7 @@ __global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
         const bool wr = p < n4 && t < ntile;  // writes B rows 2p, 2p+1
         const cplx<float> pvp = rv ? Pv[S.coup_off + p] : mk<float>(0, 0);
         cplx<float>* V = buf + tk.buf_off;
-        const int c0 = blockIdx.y * PG;
+        const int c0 = panel * PG;
         int ncol = nrhs - c0;
         if (ncol > PG) ncol = PG;
         const int k0 = 2 * p;
@@ -1288,7 +1293,7 @@ static void launch_twist_t(const Task* tasks, int ntask, const SubDesc* subs, in
     const size_t smem = twist_smem_plan(PG, F16, NT, nblk_max, nlines_max, &ns, &ring);
     cudaFuncSetAttribute(solve_twist_kernel<PG, F16, NT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(ntask * 2, (nrhs + PG - 1) / PG, 1);
+    cfg.gridDim = dim3(ntask * 2 * ((nrhs + PG - 1) / PG), 1, 1);
     cfg.blockDim = dim3(tw_threads(F16, NT), 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;

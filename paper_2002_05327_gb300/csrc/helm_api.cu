@@ -87,6 +87,7 @@ struct helm_ctx {
     helm_config cfg{};
     cudaStream_t stream = nullptr;
     bool own_stream = false;
+    cudaStream_t cstream = nullptr;  // host <-> device copies of chunked solves (created on first use)
     int device = -1;                   // the device current at helm_setup
     int prec = HELM_PREC_MIXED;
     int nsweeps = 0;
@@ -1499,32 +1500,78 @@ void solve_plan(const helm_ctx* c, int nrhs, int maxit, bool gmres, int* chunk, 
     *restart = m;
 }
 
+// Copies of a chunked solve with host buffers: every chunk's input goes on
+// the context's copy stream up front (event `in`), each chunk's output after
+// its solve (event `out` on the compute stream), so that chunk k+1's upload
+// and chunk k-1's download overlap chunk k's solve.  The destructor waits for
+// the copy stream (no copy touches the caller's buffers after the call) and
+// frees the events.
+struct ChunkCopies {
+    cudaStream_t cs = nullptr;
+    std::vector<cudaEvent_t> in, out;
+    ~ChunkCopies() {
+        if (cs) cudaStreamSynchronize(cs);
+        for (auto e : in) cudaEventDestroy(e);
+        for (auto e : out) cudaEventDestroy(e);
+    }
+};
+
 static int solve_common(helm_ctx* c, int nrhs, const void* F, void* U, int mem, double rtol,
                         int maxit, helm_stats* st, bool adjoint, bool stationary = false) {
     if (!c || !F || !U || nrhs < 1 || !(rtol > 0) || maxit < 1)
         return fail(HELM_ERR_ARG, "bad argument");
     if (!c->factored) return fail(HELM_ERR_NOT_FACTORED, "call helm_factor first");
+    if (mem != HELM_MEM_HOST && mem != HELM_MEM_DEVICE)
+        return fail(HELM_ERR_ARG, "mem must be HELM_MEM_HOST or HELM_MEM_DEVICE");
     double t0 = now_ms();
+    const bool host = mem == HELM_MEM_HOST;
     size_t bytes = (size_t)nrhs * c->Ng * 16;
     Staged f, u;
-    TRY(stage_in(c, F, bytes, mem, f, 0));
-    TRY(stage_in(c, mem == HELM_MEM_DEVICE ? U : nullptr, bytes, mem, u, 1));
+    // host buffers: device staging only here, the copies go chunk by chunk below
+    TRY(stage_in(c, host ? nullptr : F, bytes, mem, f, 0));
+    TRY(stage_in(c, host ? nullptr : U, bytes, mem, u, 1));
     TRY(ensure_bvec(c, nrhs));
-    if (adjoint) {
-        // A^H lam = g  <=>  A conj(lam) = conj(g)  (A^T = A)
-        CK(cudaMemcpyAsync(c->bvec, f.ptr, bytes, cudaMemcpyDeviceToDevice, c->stream));
-        { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_conj(c->bvec, (int64_t)nrhs * c->Ng, c->stream); }
-    } else {
-        { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_scale_J(c->P, c->gwin, f.ptr, c->bvec, nrhs, false, c->stream); }
-    }
     int chunk = nrhs, restart = c->cfg.restart;
     solve_plan(c, nrhs, maxit, !stationary, &chunk, &restart);
+    const int nchunk = (nrhs + chunk - 1) / chunk;
+    ChunkCopies cc;
+    if (host) {
+        if (!c->cstream) CK(cudaStreamCreateWithFlags(&c->cstream, cudaStreamNonBlocking));
+        cc.cs = c->cstream;
+        for (int k = 0; k < nchunk; ++k) {
+            cudaEvent_t a, b;
+            CK(cudaEventCreateWithFlags(&a, cudaEventDisableTiming));
+            cc.in.push_back(a);
+            CK(cudaEventCreateWithFlags(&b, cudaEventDisableTiming));
+            cc.out.push_back(b);
+        }
+        // the compute stream's earlier work on the staging buffers precedes the uploads
+        CK(cudaEventRecord(cc.out[0], c->stream));
+        CK(cudaStreamWaitEvent(cc.cs, cc.out[0], 0));
+        for (int k = 0; k < nchunk; ++k) {
+            const size_t off = (size_t)k * chunk * c->Ng, nb = (size_t)std::min(chunk, nrhs - k * chunk) * c->Ng * 16;
+            CK(cudaMemcpyAsync(f.ptr + off, static_cast<const cplx<double>*>(F) + off, nb, cudaMemcpyHostToDevice,
+                               cc.cs));
+            CK(cudaEventRecord(cc.in[k], cc.cs));
+        }
+    }
     int rc = HELM_OK;
     helm_stats acc{};
-    for (int r0 = 0; r0 < nrhs; r0 += chunk) {
-        const int nr = std::min(chunk, nrhs - r0);
-        helm_stats one{};
+    for (int k = 0; k < nchunk; ++k) {
+        const int r0 = k * chunk, nr = std::min(chunk, nrhs - r0);
         const size_t off = (size_t)r0 * c->Ng;
+        if (host) CK(cudaStreamWaitEvent(c->stream, cc.in[k], 0));
+        if (adjoint) {
+            // A^H lam = g  <=>  A conj(lam) = conj(g)  (A^T = A)
+            CK(cudaMemcpyAsync(c->bvec + off, f.ptr + off, (size_t)nr * c->Ng * 16, cudaMemcpyDeviceToDevice,
+                               c->stream));
+            ProfScope ps_(c, HELM_K_KRYLOV, 1);
+            launch_conj(c->bvec + off, (int64_t)nr * c->Ng, c->stream);
+        } else {
+            ProfScope ps_(c, HELM_K_KRYLOV, 1);
+            launch_scale_J(c->P, c->gwin, f.ptr + off, c->bvec + off, nr, false, c->stream);
+        }
+        helm_stats one{};
         const int rci = stationary ? stationary_dev(c, nr, c->bvec + off, u.ptr + off, rtol, maxit, &one)
                                    : gmres_dev(c, nr, c->bvec + off, u.ptr + off, rtol, maxit, &one, restart);
         if (rci != HELM_OK && rci != HELM_ERR_NO_CONVERGENCE) return rci;
@@ -1534,12 +1581,18 @@ static int solve_common(helm_ctx* c, int nrhs, const void* F, void* U, int mem, 
         acc.resid = std::max(acc.resid, one.resid);
         acc.levels = one.levels;
         acc.solves = one.solves;
+        if (adjoint) launch_conj(u.ptr + off, (int64_t)nr * c->Ng, c->stream);
+        if (host) {
+            CK(cudaEventRecord(cc.out[k], c->stream));
+            CK(cudaStreamWaitEvent(cc.cs, cc.out[k], 0));
+            CK(cudaMemcpyAsync(static_cast<cplx<double>*>(U) + off, u.ptr + off, (size_t)nr * c->Ng * 16,
+                               cudaMemcpyDeviceToHost, cc.cs));
+        }
     }
     if (st) *st = acc;
-    if (rc != HELM_OK && rc != HELM_ERR_NO_CONVERGENCE) return rc;
     std::string msg = g_last_error;
-    if (adjoint) launch_conj(u.ptr, (int64_t)nrhs * c->Ng, c->stream);
-    TRY(stage_out(c, U, u, bytes, mem));
+    if (host) CK(cudaStreamSynchronize(cc.cs));
+    TRY(stage_out(c, U, u, bytes, HELM_MEM_DEVICE));  // waits for the compute stream, checks the device
     if (st) {
         st->t_factor_ms = c->t_factor_ms;
         st->t_solve_ms = now_ms() - t0;
@@ -1756,6 +1809,7 @@ void helm_destroy(helm_ctx* c) {
     resolve_profile(c);
     for (auto e : c->event_pool) cudaEventDestroy(e);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    if (c->cstream) cudaStreamDestroy(c->cstream);
     delete c;
 }
 

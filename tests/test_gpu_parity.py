@@ -277,6 +277,40 @@ def test_release_and_refactor_give_the_same_gradient(H):
     ctx.close()
 
 
+def test_chunked_solve_with_host_buffers(H):
+    """helm_solve with host buffers and a device-memory cap that forces the
+    batch into chunks: the chunks' uploads and downloads run on a copy stream
+    beside the other chunks' solves.  Every right-hand side must still match
+    the global direct solve, and the device-pointer call the same way."""
+    import torch
+    wl = W.small_2d(nx=60, ny=52, nbx=4, nby=3, nrhs=8)
+    ref = OH.solve_global(wl)
+    base = _ctx(H, wl, 1)  # complex64: the factor holds no transient array beyond its own
+    factored = H.helm_device_bytes(base)
+    H.helm_solve(base, wl.f, rtol=1e-10, maxit=80)
+    need = H.helm_device_bytes(base) - factored  # staging, sources, window buffers, Krylov vectors
+    base.close()
+    chunked = None
+    for frac in (0.7, 0.55, 0.4, 0.3):
+        ctx = _ctx(H, wl, 1, max_device_bytes=factored + int(need * frac))
+        try:
+            u, st = H.helm_solve(ctx, wl.f, rtol=1e-10, maxit=80)
+        except H.HelmError as e:
+            assert e.code == H.HELM_ERR_OOM
+            ctx.close()
+            continue
+        if st["applications"] > st["iters"] + 1:  # more than one GMRES run
+            chunked = (ctx, u, st)
+            break
+        ctx.close()
+    assert chunked is not None, "no cap gave a chunked solve"
+    ctx, u, st = chunked
+    assert_close(u, ref, 1e-6, 1e-6, ("chunked, host buffers", st))
+    ud, _ = H.helm_solve(ctx, torch.from_numpy(wl.f).cuda(), rtol=1e-10, maxit=80)
+    assert_close(ud.cpu().numpy(), ref, 1e-6, 1e-6, "chunked, device buffers")
+    ctx.close()
+
+
 def test_errors_are_reported(H):
     wl = W.small_2d()
     with pytest.raises(H.HelmError) as e:

@@ -28,7 +28,7 @@ import numpy as np
 __all__ = [
     "Workload", "uniform_cuts", "random_cuts", "gaussian_sources", "point_sources",
     "constant_medium", "layered_medium", "smooth_random_medium", "config", "small_2d",
-    "small_3d", "two_layer_2d", "CONFIG_NAMES",
+    "small_3d", "two_layer_2d", "iter_r3_3d", "CONFIG_NAMES",
 ]
 
 
@@ -238,6 +238,31 @@ def iter_const_2d(cells: int, nb: int, freq: float, pml: int = 30, overlap: int 
     f = point_sources(n, pml, h, [(ix, iy) for ix in idx for iy in idx]).sum(axis=0, keepdims=True)
     return Workload(f"2d-const-{cells}sq-{nb}x{nb}-iter", 2, n, h, 2 * np.pi * freq, pml, 50.0, 2,
                     (nb, nb), (uniform_cuts(cells, nb), uniform_cuts(cells, nb)), overlap, pml, m, f)
+
+
+def iter_r3_3d(nb: int, box: int = 16, pml: int = 6, overlap: int = 2, sub_pml: int = 6,
+               seed: int = 53) -> Workload:
+    """A scaled stand-in of the 3D five-layer experiment of Section 5.2
+    (Table tab:iter_R3): the unit cube in nb^3 equal subdomains of box^3 cells
+    (box = 16 and a 6-cell PML where the paper has 30 and 12, so that a plane
+    block of a window stays within 32 x 32 nodes), five equal-depth layers of
+    speed 1.0 .. 2.0 along z (the paper's speeds are given only in a figure), a
+    frequency of 8 points per wavelength at the slowest speed, and
+    N_RHS = 2 (3 nb - 2) point sources on the plane z = 0.85 at seeded (x, y)
+    positions."""
+    cells = box * nb
+    n, h = (cells, cells, cells), 1.0 / cells
+    m = layered_medium(n, pml, h, speeds=(1.0, 1.25, 1.5, 1.75, 2.0), perturb=0.0, depth_axis=2)
+    omega = 2 * np.pi * 1.0 / (8 * h)
+    rng = np.random.default_rng(seed)
+    nrhs = 2 * (3 * nb - 2)
+    xy = rng.uniform(0.1, 0.9, size=(nrhs, 2))
+    iz = int(round(0.85 / h - 0.5)) + pml
+    nodes = [(int(round(x / h - 0.5)) + pml, int(round(y / h - 0.5)) + pml, iz) for x, y in xy]
+    f = point_sources(n, pml, h, nodes)
+    cuts = tuple(uniform_cuts(cells, nb) for _ in range(3))
+    return Workload(f"3d-5layer-{cells + 2 * pml}cube-{nb}x{nb}x{nb}-{nrhs}rhs", 3, n, h, omega, pml, 50.0, 2,
+                    (nb, nb, nb), cuts, overlap, sub_pml, m, f)
 
 
 def small_2d(nx=48, ny=40, nbx=3, nby=2, pml=8, overlap=4, sub_pml=8, nrhs=2,

@@ -1049,8 +1049,15 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
     int total = 0, apps = 0;
     double maxres = 0;
     bool conv = false;
-    while (true) {
-        { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_apply_A(c->P, c->stc_d, b, x, w, nrhs, c->stream); }
+    for (bool first = true;; first = false) {
+        // r = b - A x: b itself while x is still zero
+        if (first) {
+            ProfScope ps_(c, HELM_K_KRYLOV, 1);
+            launch_to_ff(b, w, (int64_t)nrhs * Ng, c->stream);
+        } else {
+            ProfScope ps_(c, HELM_K_KRYLOV, 1);
+            launch_apply_A(c->P, c->stc_d, b, x, w, nrhs, c->stream);
+        }
         std::vector<double> beta(nrhs);
         TRY(norms(w, beta));
         maxres = 0;

@@ -272,6 +272,8 @@ void launch_combo_dots(float4* w, const float4* const* U, int nv, const cplx<dou
                        bool want_dots, cplx<double>* out, cplx<double>* partial, int nblk, cudaStream_t st);
   // v[c] = src[c] * s[c]
 void launch_conj(cplx<double>* v, int64_t count, cudaStream_t st);
+// w = b converted to float-float (float4 per entry), count entries.
+void launch_to_ff(const cplx<double>* b, float4* w, int64_t count, cudaStream_t st);
 void launch_gradient(const DevProblem& P, const Win<double>& g, const cplx<double>* U,
                      const cplx<double>* L, int nsrc, double* grad, cudaStream_t st);
 

@@ -461,6 +461,18 @@ void launch_conj(cplx<double>* v, int64_t count, cudaStream_t st) {
     conj_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(v, count);
 }
 
+// w = b in float-float form (the residual b - A x of a zero x): one entry per
+// thread, grid-strided.
+__global__ void to_ff_kernel(const cplx<double>* __restrict__ b, float4* __restrict__ w, int64_t count) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        st_c(w + i, ld_c(b + i));
+}
+
+void launch_to_ff(const cplx<double>* b, float4* w, int64_t count, cudaStream_t st) {
+    const int64_t blocks = std::min<int64_t>((count + 255) / 256, 152 * 16);
+    to_ff_kernel<<<(unsigned)blocks, 256, 0, st>>>(b, w, count);
+}
+
 __global__ void gradient_kernel(DevProblem P, Win<double> w, const cplx<double>* __restrict__ U,
                                 const cplx<double>* __restrict__ L, int nsrc, double* grad) {
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];

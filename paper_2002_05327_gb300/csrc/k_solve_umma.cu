@@ -1017,17 +1017,20 @@ __global__ void __launch_bounds__(tw_threads(F16, NT)) solve_twist_kernel(
                     if (lane == 0) sr[warp * PG + c] = wmx;
                 }
                 if (epi_any(bad, kTwEpiThreads)) return false;
-#pragma unroll
-                for (int c = 0; c < PG; ++c) {
+                {
+                    // lane c < PG combines column c over the epilogue warps; the
+                    // exponents then reach every lane by shuffles
+                    const int cl = lane < PG ? lane : 0;
                     uint32_t mx = 0;
 #pragma unroll
-                    for (int w = 0; w < kTwEpi; ++w) mx = max(mx, sr[w * PG + c]);
+                    for (int w = 0; w < kTwEpi; ++w) mx = max(mx, sr[w * PG + cl]);
                     int sc = 0;
                     if (mx != 0 && mx < 0x7F800000u) {
                         sc = 13 - ((int)((mx >> 23) & 0xFF) - 127);
                         sc = sc < -100 ? -100 : (sc > 100 ? 100 : sc);
                     }
-                    sbv[c] = sc;
+#pragma unroll
+                    for (int c = 0; c < PG; ++c) sbv[c] = __shfl_sync(0xffffffffu, sc, c);
                 }
                 if (wr) {
                     __half* bh = reinterpret_cast<__half*>(bl);

@@ -46,7 +46,10 @@ METRIC = "RHS solves/sec at 1e-6 rel. L2 (mixed vs plain FP64 GPU DDM); %tensor/
 # launches of one step, from one single-pass ncu capture of the bench command's launch
 # list (dram__bytes_read.sum + dram__bytes_write.sum), per (workload, kernel).  An entry
 # is removed when the kernel changes.
-SOLVE_TRAFFIC_BYTES_PER_LAUNCH = {}
+SOLVE_TRAFFIC_BYTES_PER_LAUNCH = {
+    # 60 consecutive launches (one DDM application, 128 right-hand sides per chunk)
+    ("2d-smooth-2088x1576-12x9-256rhs", "solve_twist_kernel"): 2.0598e9,
+}
 UNIT = "RHS/s"
 
 

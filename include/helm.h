@@ -137,6 +137,14 @@ typedef struct {
                            refused with HELM_ERR_OOM before cudaMalloc is called, and
                            helm_setup refuses a problem whose grid arrays alone exceed it
                            before touching the device. */
+    int32_t algorithm;  /* 0 = the diagonal sweeps (Algorithm 3.1 in 2D, 4.1 in 3D, with
+                           sweep_order); 1 = the additive DDM of Section 2.2 (Algorithm 2.1 in
+                           2D, 2.2 in 3D): at every step s = 0 .. sum_k (nb_k - 1) every
+                           subdomain solves with the transfers that left its neighbours at
+                           step s - |d|_1 (all 3^n - 1 directions d), and the solution sums the
+                           box-weighted local solutions of every step.  Same kernels; about
+                           (sum_k (nb_k - 1) + 1) / 2^n times the solves of the sweeps.  Other
+                           values return HELM_ERR_ARG. */
 } helm_config;
 
 typedef struct {

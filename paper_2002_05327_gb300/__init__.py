@@ -50,7 +50,8 @@ class helm_config(ctypes.Structure):
                 ("restart", ctypes.c_int32), ("verbose", ctypes.c_int32),
                 ("stream", ctypes.c_void_p), ("profile", ctypes.c_int32),
                 ("tc_kernel", ctypes.c_int32), ("wait_limit", ctypes.c_int32),
-                ("sweep_order", ctypes.c_int32), ("max_device_bytes", ctypes.c_int64)]
+                ("sweep_order", ctypes.c_int32), ("max_device_bytes", ctypes.c_int64),
+                ("algorithm", ctypes.c_int32)]
 
 
 KERNEL_CLASSES = ("factor", "solve", "gather", "assemble", "krylov")
@@ -201,7 +202,7 @@ class Context:
 def helm_setup(ndim, n, h, omega, m, pml_width, sigma0, nb, overlap, power=2,
                form=HELM_PML_LITERAL, cuts=None, sub_pml=0, precision=HELM_PREC_MIXED,
                rhs_panel=0, restart=30, verbose=0, stream=None, profile=0,
-               tc_kernel=0, wait_limit=0, sweep_order=0, max_device_bytes=0) -> Context:
+               tc_kernel=0, wait_limit=0, sweep_order=0, max_device_bytes=0, algorithm=0) -> Context:
     L = lib()
     nn = (ctypes.c_int64 * 3)(*(list(n) + [1] * (3 - len(n))))
     m = np.ascontiguousarray(m, dtype=np.float64)
@@ -220,7 +221,7 @@ def helm_setup(ndim, n, h, omega, m, pml_width, sigma0, nb, overlap, power=2,
     part.sub_pml = int(sub_pml)
     cfg = helm_config(int(precision), int(rhs_panel), int(restart), int(verbose),
                       ctypes.c_void_p(stream) if stream else None, int(profile), int(tc_kernel),
-                      int(wait_limit), int(sweep_order), int(max_device_bytes))
+                      int(wait_limit), int(sweep_order), int(max_device_bytes), int(algorithm))
     out = ctypes.c_void_p()
     _check(L.helm_setup(ctypes.byref(out), int(ndim), nn, float(h), float(omega),
                         m.ctypes.data_as(ctypes.c_void_p), ctypes.byref(pml), ctypes.byref(part),

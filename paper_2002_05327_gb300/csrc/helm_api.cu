@@ -461,6 +461,7 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
     if (c->cfg.restart > 63) return fail(HELM_ERR_ARG, "restart must be at most 63");
     if (c->cfg.wait_limit < -1) return fail(HELM_ERR_ARG, "wait_limit must be -1, 0 or positive");
     if (c->cfg.sweep_order != 0 && c->cfg.sweep_order != 1) return fail(HELM_ERR_ARG, "sweep_order must be 0 or 1");
+    if (c->cfg.algorithm != 0 && c->cfg.algorithm != 1) return fail(HELM_ERR_ARG, "algorithm must be 0 or 1");
     c->wait_polls = c->cfg.wait_limit == 0    ? kDefaultWaitPolls
                     : c->cfg.wait_limit == -1 ? 0u
                                               : (uint32_t)c->cfg.wait_limit;
@@ -481,7 +482,8 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
     }
     c->Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
     P.nsub = P.nb[0] * P.nb[1] * P.nb[2];
-    c->nsweeps = 1 << ndim;
+    // diagonal sweeps: 2^n sweeps; additive (Algorithm 2.1/2.2): one "sweep" index per step
+    c->nsweeps = c->cfg.algorithm == 1 ? P.nb[0] + P.nb[1] + P.nb[2] - 3 + 1 : 1 << ndim;
     // host-side checks before any device work: the medium, and the device-memory cap
     // against the grid arrays setup allocates (m in float64 and float32, the stencil)
     for (int64_t i = 0; i < c->Ng; ++i)
@@ -684,7 +686,7 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
     TRY(upload(&c->subs_d, c->subs_h.data(), c->subs_h.size() * sizeof(SubDesc), c));
     c->fac_bytes = (size_t)fac_elems * (c->prec == HELM_PREC_F64 ? 8 : 4);
 
-    // ---- routing and dependency levels of one application of Algorithm 3.1/4.1
+    // ---- routing and dependency levels of one application of Algorithm 3.1/4.1 (or 2.1/2.2)
     auto S = sweep_dirs(ndim, c->cfg.sweep_order);
     auto dirs = transfer_dirs(ndim);
     const int L = c->nsweeps, ns = P.nsub;
@@ -703,7 +705,15 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
                     ok &= J[a] >= 0 && J[a] < P.nb[a];
                 }
                 if (!ok) continue;
-                int l2 = route_of(l, d, S, ndim);
+                // the receiving sweep: the routing rules (Algorithm 3.1/4.1), or in the
+                // additive DDM the step |d|_1 later (Algorithm 2.1/2.2)
+                int l2;
+                if (c->cfg.algorithm == 1) {
+                    l2 = l + std::abs(d[0]) + std::abs(d[1]) + std::abs(d[2]);
+                    if (l2 >= L) l2 = -1;
+                } else {
+                    l2 = route_of(l, d, S, ndim);
+                }
                 if (l2 < 0) continue;
                 int r = J[0] + P.nb[0] * (J[1] + P.nb[1] * J[2]);
                 inc[(size_t)l2 * ns + r].push_back({{d[0], d[1], d[2]}, s, l});

@@ -53,7 +53,7 @@ int main(void) {
   P(helm_pml, sigma0) P(helm_pml, form) P(helm_partition, cuts) P(helm_partition, overlap)
   P(helm_partition, sub_pml) P(helm_config, stream) P(helm_stats, resid)
   P(helm_stats, t_solve_ms) P(helm_stats, levels) P(helm_stats, solves)
-  P(helm_config, profile) P(helm_config, tc_kernel) P(helm_config, wait_limit) P(helm_config, sweep_order) P(helm_config, max_device_bytes) P(helm_profile, ms) P(helm_profile, bytes) P(helm_profile, flops)
+  P(helm_config, profile) P(helm_config, tc_kernel) P(helm_config, wait_limit) P(helm_config, sweep_order) P(helm_config, max_device_bytes) P(helm_config, algorithm) P(helm_profile, ms) P(helm_profile, bytes) P(helm_profile, flops)
   printf("helm_profile %zu\n", sizeof(helm_profile));
   return 0;
 }

@@ -121,6 +121,27 @@ def test_apply_ddm_matches_algorithm(H, case, prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", [0, 1, 5])
+@pytest.mark.parametrize("case", ["2d-layered-4x3-5rhs", "2d-nonuniform-3x3", "3d-layered-3x2x2"])
+def test_additive_ddm_matches_algorithm(H, case, prec):
+    """helm_config.algorithm = 1: the additive DDM of Section 2.2 (Algorithm
+    2.1 in 2D, 2.2 in 3D), every subdomain solving at every step, equals the
+    oracle's additive() element by element; it differs from the sweeps'
+    result, so the option is in effect."""
+    wl = CASES[case]()
+    ctx = _ctx(H, wl, prec, algorithm=1)
+    u = H.helm_apply_ddm(ctx, wl.f)
+    ctx.close()
+    _, J = OH.global_operator(wl)
+    part = OD.Partition(wl)
+    ref = OD.additive(part, wl.f * J.reshape((1,) + wl.f.shape[1:]))
+    assert_close(u, ref, TOL[prec], TOL[prec], ("additive", case, prec))
+    if prec == 0:
+        assert rel(u, OD.ddm_solution(wl)) > 1e-6
+    with pytest.raises(H.HelmError):
+        H.helm_setup_workload(wl, algorithm=2)
+
+
 @pytest.mark.parametrize("prec", [0, 5])
 def test_alternative_3d_sweep_order_matches_algorithm(H, prec):
     """helm_config.sweep_order = 1 (the second 3D order of Section 4.1) equals

@@ -29,25 +29,31 @@ __device__ __forceinline__ void unflat(int64_t k, const int N[3], int g[3]) {
     g[2] = (int)(k / ((int64_t)N[0] * N[1]));
 }
 
-__global__ void scale_J_kernel(DevProblem P, Win<double> w, const cplx<double>* f,
-                               cplx<double>* b, int nrhs, int conj_in) {
+// b = J f (or J conj(f)): one thread per grid node, J = prod_a alpha_a formed
+// once and applied to every right-hand side (coalesced along the nodes for
+// each right-hand side); the FP64 products of J are not repeated per RHS.
+constexpr int kSJ = 8;  // right-hand sides per thread
+__global__ void scale_J_kernel(DevProblem P, Win<double> w, const cplx<double>* __restrict__ f,
+                               cplx<double>* __restrict__ b, int nrhs, int conj_in) {
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int c = blockIdx.y;
     if (k >= Ng) return;
     int g[3];
     unflat(k, P.N, g);
     cplx<double> J = mk<double>(1, 0);
     for (int a = 0; a < P.ndim; ++a) J = J * w.alpha_node[a][g[a]];
-    cplx<double> v = f[(int64_t)c * Ng + k];
-    if (conj_in) v = cconj(v);
-    b[(int64_t)c * Ng + k] = J * v;
+    const int c1 = min(nrhs, (int)(blockIdx.y + 1) * kSJ);
+    for (int c = blockIdx.y * kSJ; c < c1; ++c) {
+        cplx<double> v = f[(int64_t)c * Ng + k];
+        if (conj_in) v = cconj(v);
+        b[(int64_t)c * Ng + k] = J * v;
+    }
 }
 
 void launch_scale_J(const DevProblem& P, const Win<double>& g, const cplx<double>* f,
                     cplx<double>* b, int nrhs, bool conj_in, cudaStream_t st) {
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
-    dim3 grid((unsigned)((Ng + 255) / 256), nrhs);
+    dim3 grid((unsigned)((Ng + 255) / 256), (nrhs + kSJ - 1) / kSJ);
     scale_J_kernel<<<grid, 256, 0, st>>>(P, g, f, b, nrhs, conj_in ? 1 : 0);
 }
 

@@ -1065,8 +1065,11 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
             ProfScope ps_(c, HELM_K_KRYLOV, 1);
             launch_to_ff(b, w, (int64_t)nrhs * Ng, c->stream);
         } else {
-            ProfScope ps_(c, HELM_K_KRYLOV, 1);
-            launch_apply_A(c->P, c->stc_d, b, x, w, nrhs, c->stream);
+            // x in float-float form first (into u_0's buffer, free until the swap
+            // below): the operator product then reads no FP64 neighbours
+            ProfScope ps_(c, HELM_K_KRYLOV, 2);
+            launch_to_ff(x, fv(1), (int64_t)nrhs * Ng, c->stream);
+            launch_apply_A(c->P, c->stc_d, b, static_cast<const float4*>(fv(1)), w, nrhs, c->stream);
         }
         std::vector<double> beta(nrhs);
         TRY(norms(w, beta));

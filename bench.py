@@ -497,6 +497,11 @@ def main():
                      "hbm_achieved_gbs": achieved, "hbm_frac": achieved / hbm,
                      "tflops_achieved": tflops, "tensor_frac": tflops / bf16,
                      "bytes_per_launch": sol["bytes"] / max(1, sol["launches"]),
+                     "bytes_convention": "block inverses at complex64 storage (8 bytes per entry), "
+                                         "read once per forward and once per backward pass, plus "
+                                         "b, y, y, u once per right-hand side" + (
+                                             "; the FP16 image the kernel streams holds 4 bytes "
+                                             "per entry" if args.prec == "f16" else ""),
                      "flops_per_launch": sol["flops"] / max(1, sol["launches"]),
                      "ms_per_launch": sol["ms"] / max(1, sol["launches"])},
         "kernel_time_share": kshare,

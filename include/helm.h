@@ -273,7 +273,10 @@ enum helm_kernel_class {
  * recorded on the context's stream around each launch (only when
  * helm_config.profile = 1, else 0); bytes and flops are the algorithmic
  * DRAM bytes and floating-point operations of those launches (factor and
- * solve classes: dense block reads/writes and complex multiply-adds). */
+ * solve classes: dense block reads/writes and complex multiply-adds; the
+ * solves count each block inverse at the factors' complex storage size, 8
+ * bytes per entry for complex64 and 16 for complex128, also where the
+ * tensor-core kernel streams a 4-byte FP16 image of it). */
 typedef struct {
     int64_t launches[8];
     double ms[8];

@@ -919,10 +919,11 @@ int apply_ddm_dev(helm_ctx* c, int nrhs, const VB* b, VB* U) {
         for (const Task& tk : c->levels[lv]) {
             const SubDesc& S = c->subs_h[tk.sub];
             const double n = S.nblk, nl = S.nlines, passes = 2.0 * nl - 1.0;
-            // block inverses once per pass (FP16 image: 4 bytes per complex entry) + b in, y out,
-            // y in, u out
-            const double fes = (c->umma_twist && c->f16) ? 4.0 : es;
-            sbytes += passes * n * n * fes + 4.0 * nl * n * nrhs * es;
+            // block inverses once per pass, counted at the factors' complex storage size
+            // (8 bytes per entry for complex64, 16 for complex128) whatever image the kernel
+            // streams (the FP16 tensor-core image holds 4 bytes per entry), + b in, y out, y in,
+            // u out
+            sbytes += passes * n * n * es + 4.0 * nl * n * nrhs * es;
             sflops += passes * n * n * nrhs * 8.0;
         }
         if (c->prec == HELM_PREC_F64) {

@@ -1148,7 +1148,10 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
                 CK(cudaStreamSynchronize(c->stream));
                 return HELM_OK;
             };
-            { ProfScope ps_(c, HELM_K_KRYLOV, 2); launch_mdots(c->vptr_d, k + 1, w, Ng, nrhs, c->small_d, c->partial_d, nblk, c->stream); }
+            {
+                ProfScope ps_(c, HELM_K_KRYLOV, mdots_launches(k + 1));
+                launch_mdots(c->vptr_d, k + 1, w, Ng, nrhs, c->small_d, c->partial_d, nblk, c->stream);
+            }
             TRY(fetch((size_t)(k + 1) * nrhs));
             CK(take_dots());
             std::vector<double> wn(nrhs);
@@ -1173,7 +1176,11 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
                 for (int r = 0; r < nrhs; ++r) wn[r] = std::sqrt(std::max(0.0, hd[r].re));
             } else {
                 { ProfScope ps_(c, HELM_K_KRYLOV, 1); launch_mcombo(w, c->vptr_d, k + 1, c->small_d, Ng, nrhs, 1.0, c->stream); }
-                { ProfScope ps_(c, HELM_K_KRYLOV, 2); launch_mdots(c->vptr_d, k + 1, w, Ng, nrhs, c->small_d + coef.size(), c->partial_d, nblk, c->stream); }
+                {
+                    ProfScope ps_(c, HELM_K_KRYLOV, mdots_launches(k + 1));
+                    launch_mdots(c->vptr_d, k + 1, w, Ng, nrhs, c->small_d + coef.size(), c->partial_d, nblk,
+                                 c->stream);
+                }
                 CK(cudaMemcpyAsync(hd.data(), c->small_d + coef.size(), coef.size() * 16, cudaMemcpyDeviceToHost,
                                    c->stream));
                 CK(cudaStreamSynchronize(c->stream));

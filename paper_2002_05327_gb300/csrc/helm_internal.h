@@ -262,6 +262,7 @@ void launch_norms2(const VV* v, int64_t n, int nrhs, cplx<double>* out, cplx<dou
 // fused over nv float-float vectors given as a device array of pointers (nv <= 64)
 void launch_mdots(const float4* const* V, int nv, const float4* w, int64_t n, int nrhs, cplx<double>* out,
                   cplx<double>* partial, int nblk, cudaStream_t st);  // out[i*nrhs+c] = <V_i[c], w[c]>
+int mdots_launches(int nv);  // kernel launches launch_mdots makes for nv vectors
 template <typename VW>
 void launch_mcombo(VW* w, const float4* const* V, int nv, const cplx<double>* coef, int64_t n, int nrhs,
                    double sign, cudaStream_t st);  // w[c] += sign * sum_i coef[i*nrhs+c] V_i[c]

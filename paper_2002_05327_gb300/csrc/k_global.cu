@@ -99,25 +99,49 @@ void launch_stencil_ff(const DevProblem& P, const Win<double>& g, const double* 
 // alpha is 1, so the coefficients are real (their imaginary parts are exact
 // zeros) and each term needs two products, not four.
 constexpr int kAR = 2;  // right-hand sides per thread of the operator product
-template <typename VU, typename VR>
-__device__ __forceinline__ void apply_A_node(const DevProblem& P, int64_t Ng, const float4* __restrict__ stc,
+// Grid coordinates of node k of an NDIM-dimensional grid, in 32-bit integer
+// arithmetic where the grid has fewer than 2^32 nodes (uniform over a launch);
+// a 64-bit division is a long software sequence on the GPU.
+template <int NDIM>
+__device__ __forceinline__ void unflat_nd(int64_t k, const int N[3], bool small, int g[3]) {
+    if (small) {
+        const uint32_t kk = (uint32_t)k, n0 = (uint32_t)N[0];
+        const uint32_t q = kk / n0;
+        g[0] = (int)(kk - q * n0);
+        if (NDIM == 2) {
+            g[1] = (int)q;
+            g[2] = 0;
+        } else {
+            const uint32_t n1 = (uint32_t)N[1], q2 = q / n1;
+            g[1] = (int)(q - q2 * n1);
+            g[2] = (int)q2;
+        }
+    } else {
+        unflat(k, N, g);
+    }
+}
+// NDIM is the grid's dimension: the neighbour arrays hold exactly the 2 NDIM
+// stencil neighbours, so that they stay in registers.
+template <int NDIM, typename VU, typename VR>
+__device__ __forceinline__ void apply_A_node(const DevProblem& P, int64_t Ng, bool small,
+                                             const float4* __restrict__ stc,
                                              const cplx<double>* __restrict__ b, const VU* __restrict__ u,
                                              VR* __restrict__ r, int nrhs, int64_t k, int c0) {
+    constexpr int NB = 2 * NDIM;
     int g[3];
-    unflat(k, P.N, g);
-    const int npt = 1 + 2 * P.ndim;
+    unflat_nd<NDIM>(k, P.N, small, g);
+    const int npt = 1 + NB;
     const float4* sk = stc + k * npt;
-    // neighbour slots 2a (+1 along axis a) and 2a+1 (-1), fixed so that the
-    // arrays stay in registers; a slot off the grid (Dirichlet) is skipped
-    int64_t off[6];
-    bool have[6];
-    ff cr[6], ci[6];
+    // neighbour slots 2a (+1 along axis a) and 2a+1 (-1); a slot off the grid
+    // (Dirichlet) is skipped
+    int64_t off[NB];
+    bool have[NB];
+    ff cr[NB], ci[NB];
     int64_t stride = 1;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const bool on = a < P.ndim;
-        have[2 * a] = on && g[a] + 1 < P.N[a];
-        have[2 * a + 1] = on && g[a] > 0;
+    for (int a = 0; a < NDIM; ++a) {
+        have[2 * a] = g[a] + 1 < P.N[a];
+        have[2 * a + 1] = g[a] > 0;
         off[2 * a] = stride;
         off[2 * a + 1] = -stride;
         const float4 qp = have[2 * a] ? sk[1 + 2 * a] : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -126,22 +150,22 @@ __device__ __forceinline__ void apply_A_node(const DevProblem& P, int64_t Ng, co
         ci[2 * a] = {qp.z, qp.w};
         cr[2 * a + 1] = {qm.x, qm.y};
         ci[2 * a + 1] = {qm.z, qm.w};
-        if (on) stride *= P.N[a];
+        stride *= P.N[a];
     }
     const float4 q0 = sk[0];
     const ff dr = {q0.x, q0.y}, di = {q0.z, q0.w};
     bool real = di.hi == 0.f;
 #pragma unroll
-    for (int i = 0; i < 6; ++i) real = real && ci[i].hi == 0.f;
+    for (int i = 0; i < NB; ++i) real = real && ci[i].hi == 0.f;
     // loads of both right-hand sides first
-    cff u0[kAR], un[kAR][6], bv[kAR];
+    cff u0[kAR], un[kAR][NB], bv[kAR];
 #pragma unroll
     for (int j = 0; j < kAR; ++j) {
         const int c = c0 + j < nrhs ? c0 + j : c0;
         const VU* uc = u + (int64_t)c * Ng + k;
         u0[j] = ld_c(uc);
 #pragma unroll
-        for (int i = 0; i < 6; ++i) un[j][i] = have[i] ? ld_c(uc + off[i]) : cff{{0.f, 0.f}, {0.f, 0.f}};
+        for (int i = 0; i < NB; ++i) un[j][i] = have[i] ? ld_c(uc + off[i]) : cff{{0.f, 0.f}, {0.f, 0.f}};
         bv[j] = b ? ld_c(b + (int64_t)c * Ng + k) : cff{{0.f, 0.f}, {0.f, 0.f}};
     }
 #pragma unroll
@@ -156,7 +180,7 @@ __device__ __forceinline__ void apply_A_node(const DevProblem& P, int64_t Ng, co
             acc_mul(ai, ff_neg(di), u0[j].re);
         }
 #pragma unroll
-        for (int i = 0; i < 6; ++i) {
+        for (int i = 0; i < NB; ++i) {
             if (!have[i]) continue;
             acc_mul(ar, ff_neg(cr[i]), un[j][i].re);
             acc_mul(ai, ff_neg(cr[i]), un[j][i].im);
@@ -169,14 +193,16 @@ __device__ __forceinline__ void apply_A_node(const DevProblem& P, int64_t Ng, co
     }
 }
 
-template <typename VU, typename VR>
-__global__ void apply_A_kernel(DevProblem P, const float4* __restrict__ stc, const cplx<double>* __restrict__ b,
-                               const VU* __restrict__ u, VR* __restrict__ r, int nrhs) {
+template <int NDIM, typename VU, typename VR>
+__global__ void __launch_bounds__(256, 2)
+    apply_A_kernel(DevProblem P, const float4* __restrict__ stc, const cplx<double>* __restrict__ b,
+                   const VU* __restrict__ u, VR* __restrict__ r, int nrhs) {
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
+    const bool small = Ng <= (int64_t)UINT32_MAX;
     // node ranges along grid y, strided past the 65535-block limit
     for (int64_t kb = blockIdx.y; kb * blockDim.x < Ng; kb += gridDim.y) {
         const int64_t k = kb * blockDim.x + threadIdx.x;
-        if (k < Ng) apply_A_node(P, Ng, stc, b, u, r, nrhs, k, blockIdx.x * kAR);
+        if (k < Ng) apply_A_node<NDIM>(P, Ng, small, stc, b, u, r, nrhs, k, blockIdx.x * kAR);
     }
 }
 
@@ -185,7 +211,10 @@ void launch_apply_A(const DevProblem& P, const float4* stc, const cplx<double>* 
                     cudaStream_t st) {
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
     dim3 grid((nrhs + kAR - 1) / kAR, (unsigned)std::min<int64_t>((Ng + 255) / 256, 65535));
-    apply_A_kernel<VU, VR><<<grid, 256, 0, st>>>(P, stc, b, u, r, nrhs);
+    if (P.ndim == 2)
+        apply_A_kernel<2, VU, VR><<<grid, 256, 0, st>>>(P, stc, b, u, r, nrhs);
+    else
+        apply_A_kernel<3, VU, VR><<<grid, 256, 0, st>>>(P, stc, b, u, r, nrhs);
 }
 template void launch_apply_A<cplx<double>, cplx<double>>(const DevProblem&, const float4*, const cplx<double>*,
                                                          const cplx<double>*, cplx<double>*, int, cudaStream_t);
@@ -212,41 +241,42 @@ __global__ void dots_final_kernel(const cplx<double>* partial, int nblk, int cou
 // ---- fused multi-vector kernels of classical Gram-Schmidt: one pass over w
 // and every V_i (V given as a device array of pointers to float-float vectors)
 
-__global__ void __launch_bounds__(DOT_NT, 2) mdots_partial_kernel(const float4* const* __restrict__ V, int nv,
+// NVB vectors per block (a compile-time count, so that the per-vector
+// accumulators take only the registers they need); block z of the launch takes
+// V_{ibase + z NVB} ... V_{ibase + z NVB + NVB - 1}.
+template <int NVB>
+__global__ void __launch_bounds__(DOT_NT, 2) mdots_partial_kernel(const float4* const* __restrict__ V, int ibase,
                                                                    const float4* __restrict__ w, int64_t n,
                                                                    int nrhs, cplx<double>* partial, int nblk) {
-    __shared__ ff sr[8][DOT_NT / 32], si[8][DOT_NT / 32];
-    __shared__ const float4* svp[8];
-    const int blk = blockIdx.x, c = blockIdx.y, i0 = blockIdx.z * 8;
-    const int nvb = min(8, nv - i0);
+    __shared__ ff sr[NVB][DOT_NT / 32], si[NVB][DOT_NT / 32];
+    __shared__ const float4* svp[NVB];
+    const int blk = blockIdx.x, c = blockIdx.y, i0 = ibase + (int)blockIdx.z * NVB;
+    constexpr int nvb = NVB;
     const int64_t chunk = (n + nblk - 1) / nblk;
     const int64_t k0 = (int64_t)blk * chunk, k1 = min(n, k0 + chunk);
     const float4* wc = w + (int64_t)c * n;
     if ((int)threadIdx.x < nvb) svp[threadIdx.x] = V[i0 + threadIdx.x] + (int64_t)c * n;
     __syncthreads();
-    ff ar[8], ai[8];
+    ff ar[NVB], ai[NVB];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) ar[i] = ai[i] = ff{0.f, 0.f};
+    for (int i = 0; i < NVB; ++i) ar[i] = ai[i] = ff{0.f, 0.f};
     for (int64_t k = k0 + threadIdx.x; k < k1; k += DOT_NT) {
         const cff bw = ld_c(wc + k);
-        cff av[8];
+        cff av[NVB];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            if (i < nvb) av[i] = ld_c(svp[i] + k);  // vector pointers from shared memory
+        for (int i = 0; i < NVB; ++i) av[i] = ld_c(svp[i] + k);  // vector pointers from shared memory
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if (i < nvb) {
-                // conj(v) w = (vr br + vi bi) + i (vr bi - vi br)
-                acc_mul(ar[i], av[i].re, bw.re);
-                acc_mul(ar[i], av[i].im, bw.im);
-                acc_mul(ai[i], av[i].re, bw.im);
-                acc_mul(ai[i], ff_neg(av[i].im), bw.re);
-            }
+        for (int i = 0; i < NVB; ++i) {
+            // conj(v) w = (vr br + vi bi) + i (vr bi - vi br)
+            acc_mul(ar[i], av[i].re, bw.re);
+            acc_mul(ar[i], av[i].im, bw.im);
+            acc_mul(ai[i], av[i].re, bw.im);
+            acc_mul(ai[i], ff_neg(av[i].im), bw.re);
         }
     }
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < NVB; ++i) {
         for (int o = 16; o > 0; o >>= 1) {
             ar[i] = ff_sum(ar[i], shfl_down_ff(ar[i], o));
             ai[i] = ff_sum(ai[i], shfl_down_ff(ai[i], o));
@@ -257,7 +287,7 @@ __global__ void __launch_bounds__(DOT_NT, 2) mdots_partial_kernel(const float4* 
         }
     }
     __syncthreads();
-    if (threadIdx.x < nvb) {
+    if ((int)threadIdx.x < nvb) {
         const int i = threadIdx.x;
         ff r = {0.f, 0.f}, im = {0.f, 0.f};
         for (int q = 0; q < DOT_NT / 32; ++q) {
@@ -311,10 +341,26 @@ template void launch_norms2<cplx<double>>(const cplx<double>*, int64_t, int, cpl
 template void launch_norms2<float4>(const float4*, int64_t, int, cplx<double>*, cplx<double>*, int,
                                     cudaStream_t);
 
+int mdots_launches(int nv) { return (nv >= 8 ? 1 : 0) + (nv % 8 ? 1 : 0) + 1; }
+
 void launch_mdots(const float4* const* V, int nv, const float4* w, int64_t n, int nrhs, cplx<double>* out,
                   cplx<double>* partial, int nblk, cudaStream_t st) {
-    dim3 grid(nblk, nrhs, (nv + 7) / 8);
-    mdots_partial_kernel<<<grid, DOT_NT, 0, st>>>(V, nv, w, n, nrhs, partial, nblk);
+    // groups of 8 vectors in one launch, the rest in a second
+    const int full = nv / 8, rest = nv % 8;
+    if (full > 0)
+        mdots_partial_kernel<8><<<dim3(nblk, nrhs, full), DOT_NT, 0, st>>>(V, 0, w, n, nrhs, partial, nblk);
+    const dim3 g1(nblk, nrhs, 1);
+    const int ib = full * 8;
+    switch (rest) {
+        case 1: mdots_partial_kernel<1><<<g1, DOT_NT, 0, st>>>(V, ib, w, n, nrhs, partial, nblk); break;
+        case 2: mdots_partial_kernel<2><<<g1, DOT_NT, 0, st>>>(V, ib, w, n, nrhs, partial, nblk); break;
+        case 3: mdots_partial_kernel<3><<<g1, DOT_NT, 0, st>>>(V, ib, w, n, nrhs, partial, nblk); break;
+        case 4: mdots_partial_kernel<4><<<g1, DOT_NT, 0, st>>>(V, ib, w, n, nrhs, partial, nblk); break;
+        case 5: mdots_partial_kernel<5><<<g1, DOT_NT, 0, st>>>(V, ib, w, n, nrhs, partial, nblk); break;
+        case 6: mdots_partial_kernel<6><<<g1, DOT_NT, 0, st>>>(V, ib, w, n, nrhs, partial, nblk); break;
+        case 7: mdots_partial_kernel<7><<<g1, DOT_NT, 0, st>>>(V, ib, w, n, nrhs, partial, nblk); break;
+        default: break;
+    }
     int count = nv * nrhs;
     dots_final_kernel<<<(count + 127) / 128, 128, 0, st>>>(partial, nblk, count, out);
 }
@@ -367,13 +413,19 @@ template void launch_mcombo<cplx<double>>(cplx<double>*, const float4* const*, i
 // the next Gram-Schmidt step needs of the updated w: its dots <U_i[c], w[c]>
 // with every U_i (want_dots) or its squared norm (into slot 0).  One pass over
 // w and the U_i (nv <= 8, one right-hand side per block row, a fixed chunk
-// per block as in the dot kernels); the dots are taken of w as stored.
-__global__ void __launch_bounds__(DOT_NT, 2) combo_dots_kernel(float4* w, const float4* const* __restrict__ U, int nv,
-                                  const cplx<double>* __restrict__ coef, int64_t n, int nrhs, int want_dots,
+// per block as in the dot kernels); the dots are taken of w as stored.  NV
+// and WANT_DOTS are compile-time, so that the per-vector values and
+// accumulators take only the registers they need.
+template <int NV, bool WANT_DOTS>
+__global__ void __launch_bounds__(DOT_NT, 2) combo_dots_kernel(float4* w, const float4* const* __restrict__ U,
+                                  const cplx<double>* __restrict__ coef, int64_t n, int nrhs,
                                   cplx<double>* partial, int nblk) {
-    __shared__ ff scr[8], sci[8];
-    __shared__ const float4* sup[8];
-    __shared__ ff sr[8][DOT_NT / 32], si[8][DOT_NT / 32];
+    constexpr int nv = NV;
+    constexpr bool want_dots = WANT_DOTS;
+    constexpr int NA = WANT_DOTS ? NV : 1;  // accumulators: the dots, or the norm
+    __shared__ ff scr[NV], sci[NV];
+    __shared__ const float4* sup[NV];
+    __shared__ ff sr[NA][DOT_NT / 32], si[NA][DOT_NT / 32];
     const int blk = blockIdx.x, c = blockIdx.y;
     if ((int)threadIdx.x < nv) {
         const cplx<double> a = coef[threadIdx.x * nrhs + c];
@@ -385,50 +437,44 @@ __global__ void __launch_bounds__(DOT_NT, 2) combo_dots_kernel(float4* w, const 
     const int64_t chunk = (n + nblk - 1) / nblk;
     const int64_t k0 = (int64_t)blk * chunk, k1 = min(n, k0 + chunk);
     float4* wc = w + (int64_t)c * n;
-    ff dr[8], di[8];
+    ff dr[NA], di[NA];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) dr[i] = di[i] = ff{0.f, 0.f};
+    for (int i = 0; i < NA; ++i) dr[i] = di[i] = ff{0.f, 0.f};
     for (int64_t k = k0 + threadIdx.x; k < k1; k += DOT_NT) {
         const cff w0 = ld_c(wc + k);
-        cff uv[8];
+        cff uv[NV];
 #pragma unroll
-        for (int i = 0; i < 8; ++i)
-            if (i < nv) uv[i] = ld_c(sup[i] + k);  // vector pointers from shared memory
+        for (int i = 0; i < NV; ++i) uv[i] = ld_c(sup[i] + k);  // vector pointers from shared memory
         ff ar = w0.re, ai = w0.im;
 #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-            if (i < nv) {
-                // (cr + i ci)(ur + i ui), the coefficients read from shared memory
-                const ff cr = scr[i], ci = sci[i];
-                acc_mul(ar, cr, uv[i].re);
-                acc_mul(ar, ff_neg(ci), uv[i].im);
-                acc_mul(ai, cr, uv[i].im);
-                acc_mul(ai, ci, uv[i].re);
-            }
+        for (int i = 0; i < NV; ++i) {
+            // (cr + i ci)(ur + i ui), the coefficients read from shared memory
+            const ff cr = scr[i], ci = sci[i];
+            acc_mul(ar, cr, uv[i].re);
+            acc_mul(ar, ff_neg(ci), uv[i].im);
+            acc_mul(ai, cr, uv[i].im);
+            acc_mul(ai, ci, uv[i].re);
         }
         const cff wn = {ff_norm(ar), ff_norm(ai)};
         wc[k] = make_float4(wn.re.hi, wn.re.lo, wn.im.hi, wn.im.lo);
         if (want_dots) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-                if (i < nv) {
-                    // conj(u) w = (ur wr + ui wi) + i (ur wi - ui wr)
-                    acc_mul(dr[i], uv[i].re, wn.re);
-                    acc_mul(dr[i], uv[i].im, wn.im);
-                    acc_mul(di[i], uv[i].re, wn.im);
-                    acc_mul(di[i], ff_neg(uv[i].im), wn.re);
-                }
+            for (int i = 0; i < NA; ++i) {
+                // conj(u) w = (ur wr + ui wi) + i (ur wi - ui wr)
+                acc_mul(dr[i], uv[i].re, wn.re);
+                acc_mul(dr[i], uv[i].im, wn.im);
+                acc_mul(di[i], uv[i].re, wn.im);
+                acc_mul(di[i], ff_neg(uv[i].im), wn.re);
             }
         } else {
             acc_mul(dr[0], wn.re, wn.re);
             acc_mul(dr[0], wn.im, wn.im);
         }
     }
-    const int nout = want_dots ? nv : 1;
+    constexpr int nout = NA;
     const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        if (i >= nout) break;
+    for (int i = 0; i < NA; ++i) {
         for (int o = 16; o > 0; o >>= 1) {
             dr[i] = ff_sum(dr[i], shfl_down_ff(dr[i], o));
             di[i] = ff_sum(di[i], shfl_down_ff(di[i], o));
@@ -450,10 +496,29 @@ __global__ void __launch_bounds__(DOT_NT, 2) combo_dots_kernel(float4* w, const 
     }
 }
 
+template <int NV>
+static void launch_combo_dots_nv(float4* w, const float4* const* U, const cplx<double>* coef, int64_t n, int nrhs,
+                                 bool want_dots, cplx<double>* partial, int nblk, cudaStream_t st) {
+    const dim3 grid(nblk, nrhs);
+    if (want_dots)
+        combo_dots_kernel<NV, true><<<grid, DOT_NT, 0, st>>>(w, U, coef, n, nrhs, partial, nblk);
+    else
+        combo_dots_kernel<NV, false><<<grid, DOT_NT, 0, st>>>(w, U, coef, n, nrhs, partial, nblk);
+}
+
 void launch_combo_dots(float4* w, const float4* const* U, int nv, const cplx<double>* coef, int64_t n, int nrhs,
                        bool want_dots, cplx<double>* out, cplx<double>* partial, int nblk, cudaStream_t st) {
-    dim3 grid(nblk, nrhs);
-    combo_dots_kernel<<<grid, DOT_NT, 0, st>>>(w, U, nv, coef, n, nrhs, want_dots ? 1 : 0, partial, nblk);
+    switch (nv) {
+        case 1: launch_combo_dots_nv<1>(w, U, coef, n, nrhs, want_dots, partial, nblk, st); break;
+        case 2: launch_combo_dots_nv<2>(w, U, coef, n, nrhs, want_dots, partial, nblk, st); break;
+        case 3: launch_combo_dots_nv<3>(w, U, coef, n, nrhs, want_dots, partial, nblk, st); break;
+        case 4: launch_combo_dots_nv<4>(w, U, coef, n, nrhs, want_dots, partial, nblk, st); break;
+        case 5: launch_combo_dots_nv<5>(w, U, coef, n, nrhs, want_dots, partial, nblk, st); break;
+        case 6: launch_combo_dots_nv<6>(w, U, coef, n, nrhs, want_dots, partial, nblk, st); break;
+        case 7: launch_combo_dots_nv<7>(w, U, coef, n, nrhs, want_dots, partial, nblk, st); break;
+        case 8: launch_combo_dots_nv<8>(w, U, coef, n, nrhs, want_dots, partial, nblk, st); break;
+        default: return;  // the caller keeps nv in 1 .. kComboDotsMax
+    }
     const int count = (want_dots ? nv : 1) * nrhs;
     dots_final_kernel<<<(count + 127) / 128, 128, 0, st>>>(partial, nblk, count, out);
 }

@@ -202,6 +202,34 @@ def test_gmres_reaches_global_solution(H, prec):
     ctx.close()
 
 
+@pytest.mark.parametrize("prec", [0, 5])
+def test_gmres_long_cycle(H, prec):
+    """A GMRES cycle longer than eight iterations: the Gram-Schmidt dots then
+    take the basis in a group of eight and a remainder, and the combinations
+    run unfused.  A deliberately weak preconditioner (2-cell subdomain PML,
+    overlap 2) for which the oracle's FP64 GMRES needs more than eight
+    iterations at a relative residual of 1e-10: the FP64 GPU path must need
+    that count (one more or fewer for rounding), the FP16 one more than eight
+    as well, and both must reach the direct solution."""
+    from oracle import krylov as OK
+    wl = W.small_2d(nx=64, ny=56, nbx=3, nby=3, pml=10, overlap=2, sub_pml=2, nrhs=2)
+    A, J = OH.global_operator(wl, "literal")
+    b = wl.f * J.reshape((1,) + wl.f.shape[1:])
+    Ax = lambda x: (A @ x.reshape(x.shape[0], -1).T).T.reshape(x.shape)
+    _, info = OK.gmres(Ax, b, OD.DDMPreconditioner(wl), rtol=1e-10, restart=30, maxit=30)
+    it_ref = int(np.max(info["iters"]))
+    assert it_ref >= 9, it_ref
+    ctx = _ctx(H, wl, prec)
+    x, st = H.helm_solve(ctx, wl.f, rtol=1e-10, maxit=30)
+    ctx.close()
+    if prec == 0:
+        assert abs(st["iters"] - it_ref) <= 1, (st["iters"], it_ref)
+    else:
+        assert st["iters"] >= 9, (st["iters"], it_ref)
+    assert st["resid"] <= 1e-10
+    assert_close(x, OH.solve_global(wl), 1e-6, 1e-6, ("long gmres cycle", prec))
+
+
 def test_stationary_iteration_matches_algorithm(H):
     """helm_iterate, the DDM as an iterative solver (Section 5.2.2): after three
     steps the FP64 iterate equals the oracle's u_3 and its residual; with FP16
@@ -223,9 +251,13 @@ def test_stationary_iteration_matches_algorithm(H):
     assert st["resid"] <= 1e-10
 
 
-def test_residual_matches_operator(H):
-    wl = W.small_3d(n=(12, 10, 9), nb=(2, 2, 1), pml=4, overlap=2, sub_pml=3, nrhs=2,
-                    medium="layered")
+@pytest.mark.parametrize("dim", [2, 3])
+def test_residual_matches_operator(H, dim):
+    if dim == 3:
+        wl = W.small_3d(n=(12, 10, 9), nb=(2, 2, 1), pml=4, overlap=2, sub_pml=3, nrhs=2,
+                        medium="layered")
+    else:
+        wl = W.small_2d(nx=40, ny=36, nbx=2, nby=2, pml=8, overlap=4, sub_pml=8, nrhs=3)
     ctx = _ctx(H, wl, 0)
     rng = np.random.default_rng(2)
     u = rng.standard_normal(wl.f.shape) + 1j * rng.standard_normal(wl.f.shape)

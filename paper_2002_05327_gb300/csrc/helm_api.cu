@@ -641,6 +641,7 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
         }
         if (S.nbp > 1280) return fail(HELM_ERR_ARG, "subdomain block larger than 1280 nodes");
         S.win_elems = (int64_t)S.nw[0] * S.nw[1] * S.nw[2];
+        if (S.win_elems >= ((int64_t)1 << 31)) return fail(HELM_ERR_ARG, "subdomain window of 2^31 nodes or more");
         S.fac_off = fac_elems;
         fac_elems += (int64_t)S.nlines * 2 * S.nbp * S.nbp;
         // couplings between blocks: Pv[p] = prod_{a<slow} alpha_a(node) / h^2,

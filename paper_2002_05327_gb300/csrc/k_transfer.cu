@@ -192,36 +192,51 @@ void launch_gather(const GBlock* blocks, int nblocks, const GNode* nodes, const 
 
 // ----------------------------------------------------------------------------- assembly
 constexpr int kAG = 8;  // right-hand sides per assembly thread
+// sweeps whose loads a thread issues together (complex64 windows; complex128
+// ones take one at a time, as their sums already fill the registers)
+template <typename T>
+constexpr int assemble_sweeps() { return sizeof(T) == 4 ? 2 : 1; }
 
-template <typename T, typename VU>
-__global__ void assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs,
-                                const int* __restrict__ box_of, const int64_t* __restrict__ node_buf,
-                                int nsweeps, const T* __restrict__ tab,
-                                const cplx<T>* __restrict__ buf, int64_t rstride, int nrhs, VU* U) {
+template <int NDIM, typename T, typename VU>
+__global__ void __launch_bounds__(256, 2)
+    assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs, const int* __restrict__ box_of,
+                    const int64_t* __restrict__ node_buf, int nsweeps, const T* __restrict__ tab,
+                    const cplx<T>* __restrict__ buf, int64_t rstride, int nrhs, VU* U) {
     // one thread per (global node, group of kAG right-hand sides): the boxes
     // whose cutoff reaches the node and their weights are found once, then
-    // applied to the group with independent loads
+    // applied to the group, the loads of kASW sweeps issued together
+    constexpr int kASW = assemble_sweeps<T>();
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
     const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= Ng) return;
     const int c0 = blockIdx.y * kAG;
-    const int ndim = P.ndim;
-    int g[3];
-    g[0] = (int)(k % P.N[0]);
-    g[1] = (int)((k / P.N[0]) % P.N[1]);
-    g[2] = (int)(k / ((int64_t)P.N[0] * P.N[1]));
+    int g[3] = {0, 0, 0};
+    if (Ng <= (int64_t)UINT32_MAX) {  // 32-bit index arithmetic (uniform over the launch)
+        const uint32_t kk = (uint32_t)k, n0 = (uint32_t)P.N[0], q = kk / n0;
+        g[0] = (int)(kk - q * n0);
+        if (NDIM == 2) {
+            g[1] = (int)q;
+        } else {
+            const uint32_t n1 = (uint32_t)P.N[1], q2 = q / n1;
+            g[1] = (int)(q - q2 * n1);
+            g[2] = (int)q2;
+        }
+    } else {
+        g[0] = (int)(k % P.N[0]);
+        g[1] = (int)((k / P.N[0]) % P.N[1]);
+        g[2] = (int)(k / ((int64_t)P.N[0] * P.N[1]));
+    }
     // candidate boxes per axis in fixed slots: 0 the own box (cutoff 1), 1 the
     // box above and 2 the box below, each with the weight of its cutoff at this
     // node (0 where its cutoff does not reach)
-    int cb[3][3];
-    T cw[3][3];
+    int cb[NDIM][3];
+    T cw[NDIM][3];
     int off = 0;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        cb[a][0] = cb[a][1] = cb[a][2] = 0;
+    for (int a = 0; a < NDIM; ++a) {
+        cb[a][1] = cb[a][2] = 0;
         cw[a][0] = T(1);
         cw[a][1] = cw[a][2] = T(0);
-        if (a >= ndim) continue;
         const int i0 = box_of[off + g[a]];
         off += P.N[a];
         cb[a][0] = i0;
@@ -245,10 +260,13 @@ __global__ void assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs,
             }
         }
     }
-    // boxes with a non-zero weight, in a fixed order: (window offset of the node, weight)
-    constexpr int kMaxBox = 8;
+    // boxes with a non-zero weight, in a fixed order: (window offset of the
+    // node, weight).  Where every box is at least 2d wide, at most 2^NDIM
+    // boxes reach a node; narrower boxes (down to d + 2) let both neighbours
+    // of an axis reach it: 9 in 2D, all kept; in 3D the first 8 are kept
+    constexpr int kMaxBox = NDIM == 2 ? 9 : 8;
     int sb[kMaxBox];
-    int64_t lib[kMaxBox];
+    int lib[kMaxBox];  // window offsets (a window holds fewer than 2^31 nodes)
     T wb[kMaxBox];
     int nbx = 0;
 #pragma unroll
@@ -262,15 +280,14 @@ __global__ void assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs,
 #pragma unroll
         for (int i1 = 0; i1 < 3; ++i1)
 #pragma unroll
-            for (int i2 = 0; i2 < 3; ++i2) {
-                const T wgt = cw[0][i0] * cw[1][i1] * cw[2][i2];
+            for (int i2 = 0; i2 < (NDIM == 3 ? 3 : 1); ++i2) {
+                const T wgt = NDIM == 3 ? cw[0][i0] * cw[1][i1] * cw[NDIM - 1][i2] : cw[0][i0] * cw[1][i1] * T(1);
                 if (wgt == T(0) || nbx >= kMaxBox) continue;
-                const int s = cb[0][i0] + P.nb[0] * (cb[1][i1] + P.nb[1] * cb[2][i2]);
+                const int s = cb[0][i0] + P.nb[0] * (cb[1][i1] + (NDIM == 3 ? P.nb[1] * cb[NDIM - 1][i2] : 0));
                 const SubDesc& S = subs[s];
-                int64_t li = 0;
+                int li = 0;
 #pragma unroll
-                for (int a = 2; a >= 0; --a)
-                    if (a < ndim) li = li * S.nw[a] + (g[a] - S.lo[a]);
+                for (int a = NDIM - 1; a >= 0; --a) li = li * S.nw[a] + (g[a] - S.lo[a]);
 #pragma unroll
                 for (int ib = 0; ib < kMaxBox; ++ib)  // register-resident list: static indices
                     if (ib == nbx) {
@@ -293,21 +310,30 @@ __global__ void assemble_kernel(DevProblem P, const SubDesc* __restrict__ subs,
 #pragma unroll
     for (int ib = 0; ib < kMaxBox; ++ib) {
         if (ib >= nbx) break;
-        for (int l = 0; l < nsweeps; ++l) {
-            const int64_t ob = node_buf[(int64_t)l * P.nsub + sb[ib]];
-            if (ob < 0) continue;
-            const cplx<T>* bp = buf + ob + lib[ib] + (int64_t)c0 * rstride;
-            cplx<T> v[kAG];
+        for (int l0 = 0; l0 < nsweeps; l0 += kASW) {
+            // the loads of kASW sweeps first, then the sums in sweep order
+            int64_t ob[kASW];
+            cplx<T> v[kASW][kAG];
 #pragma unroll
-            for (int c = 0; c < kAG; ++c) v[c] = (c0 + c < nrhs) ? bp[(int64_t)c * rstride] : mk<T>(0, 0);
+            for (int q = 0; q < kASW; ++q) {
+                ob[q] = l0 + q < nsweeps ? node_buf[(int64_t)(l0 + q) * P.nsub + sb[ib]] : -1;
+                const cplx<T>* bp = buf + (ob[q] < 0 ? 0 : ob[q] + (int64_t)lib[ib] + (int64_t)c0 * rstride);
 #pragma unroll
-            for (int c = 0; c < kAG; ++c) {
-                if constexpr (kF32) {
-                    ffa::acc_add(fr[c], wb[ib] * v[c].re);
-                    ffa::acc_add(fi[c], wb[ib] * v[c].im);
-                } else {
-                    sr[c] += wb[ib] * v[c].re;
-                    si[c] += wb[ib] * v[c].im;
+                for (int c = 0; c < kAG; ++c)
+                    v[q][c] = (ob[q] >= 0 && c0 + c < nrhs) ? bp[(int64_t)c * rstride] : mk<T>(0, 0);
+            }
+#pragma unroll
+            for (int q = 0; q < kASW; ++q) {
+                if (ob[q] < 0) continue;
+#pragma unroll
+                for (int c = 0; c < kAG; ++c) {
+                    if constexpr (kF32) {
+                        ffa::acc_add(fr[c], wb[ib] * v[q][c].re);
+                        ffa::acc_add(fi[c], wb[ib] * v[q][c].im);
+                    } else {
+                        sr[c] += wb[ib] * v[q][c].re;
+                        si[c] += wb[ib] * v[q][c].im;
+                    }
                 }
             }
         }
@@ -334,8 +360,12 @@ void launch_assemble(const DevProblem& P, const SubDesc* subs, const int* box_of
     const int64_t Ng = (int64_t)P.N[0] * P.N[1] * P.N[2];
     const int nt = 256;
     dim3 grid((unsigned)((Ng + nt - 1) / nt), (nrhs + kAG - 1) / kAG);
-    assemble_kernel<T, VU><<<grid, nt, 0, st>>>(P, subs, box_of, node_buf, nsweeps, beta_tab, buf, rstride, nrhs,
-                                            U);
+    if (P.ndim == 2)
+        assemble_kernel<2, T, VU><<<grid, nt, 0, st>>>(P, subs, box_of, node_buf, nsweeps, beta_tab, buf, rstride,
+                                                       nrhs, U);
+    else
+        assemble_kernel<3, T, VU><<<grid, nt, 0, st>>>(P, subs, box_of, node_buf, nsweeps, beta_tab, buf, rstride,
+                                                       nrhs, U);
 }
 
 #define HELM_TRANSFER_INST(T, V)                                                                          \

@@ -91,8 +91,9 @@ typedef struct {
  * boxes extend over the global PML.  Each subdomain problem P_{Omega_ij} has
  * `overlap` (d) cells of zero sigma beyond an internal box face followed by
  * `sub_pml` PML cells (shifted profile, Eq. 2.3); sub_pml = 0 means
- * pml.width.  Every box must be at least overlap + 2 cells wide and every
- * window must stay inside the full grid. */
+ * pml.width.  Every box must be at least overlap + 2 cells wide (in 3D an
+ * inner box at least 2 overlap) and every window must stay inside the full
+ * grid; helm_setup returns HELM_ERR_ARG otherwise. */
 typedef struct {
     int32_t nb[3];
     const int64_t *cuts[3];

@@ -568,6 +568,11 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
             bhi[a].push_back(i == P.nb[a] - 1 ? P.N[a] : (int)(Wg + cut[i + 1]));
             if (bhi[a].back() - blo[a].back() < P.d + 2)
                 return fail(HELM_ERR_ARG, "box narrower than overlap + 2");
+            // 3D: an inner box at least 2d wide, so that the cutoffs of at most
+            // one neighbour per axis reach a node and the assembly's list of
+            // eight boxes per node holds them all
+            if (ndim == 3 && i > 0 && i + 1 < P.nb[a] && bhi[a].back() - blo[a].back() < 2 * P.d)
+                return fail(HELM_ERR_ARG, "3D inner box narrower than twice the overlap");
         }
     }
     std::vector<int> box_of;

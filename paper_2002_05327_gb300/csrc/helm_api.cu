@@ -1164,8 +1164,8 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
             if (fused) {
                 {
                     ProfScope ps_(c, HELM_K_KRYLOV, 2);
-                    launch_combo_dots(w, c->vptr_d, k + 1, c->small_d, Ng, nrhs, true, c->small_d + coef.size(),
-                                      c->partial_d, nblk, c->stream);
+                    CK(launch_combo_dots(w, c->vptr_d, k + 1, c->small_d, Ng, nrhs, true,
+                                         c->small_d + coef.size(), c->partial_d, nblk, c->stream));
                 }
                 CK(cudaMemcpyAsync(hd.data(), c->small_d + coef.size(), coef.size() * 16, cudaMemcpyDeviceToHost,
                                    c->stream));
@@ -1173,8 +1173,8 @@ int gmres_dev(helm_ctx* c, int nrhs, const cplx<double>* b, cplx<double>* x, dou
                 CK(take_dots());
                 {
                     ProfScope ps_(c, HELM_K_KRYLOV, 2);
-                    launch_combo_dots(w, c->vptr_d, k + 1, c->small_d, Ng, nrhs, false, c->small_d + coef.size(),
-                                      c->partial_d, nblk, c->stream);
+                    CK(launch_combo_dots(w, c->vptr_d, k + 1, c->small_d, Ng, nrhs, false,
+                                         c->small_d + coef.size(), c->partial_d, nblk, c->stream));
                 }
                 CK(cudaMemcpyAsync(hd.data(), c->small_d + coef.size(), nrhs * 16, cudaMemcpyDeviceToHost,
                                    c->stream));

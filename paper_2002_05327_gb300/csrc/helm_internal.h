@@ -267,10 +267,12 @@ template <typename VW>
 void launch_mcombo(VW* w, const float4* const* V, int nv, const cplx<double>* coef, int64_t n, int nrhs,
                    double sign, cudaStream_t st);  // w[c] += sign * sum_i coef[i*nrhs+c] V_i[c]
 // w[c] += sum_i coef[i*nrhs+c] U_i[c] fused with, of the updated w, the dots
-// out[i*nrhs+c] = <U_i[c], w[c]> (want_dots) or the squared norms out[c]; nv <= 8
+// out[i*nrhs+c] = <U_i[c], w[c]> (want_dots) or the squared norms out[c];
+// 1 <= nv <= kComboDotsMax, else cudaErrorInvalidValue and nothing launched
 constexpr int kComboDotsMax = 8;
-void launch_combo_dots(float4* w, const float4* const* U, int nv, const cplx<double>* coef, int64_t n, int nrhs,
-                       bool want_dots, cplx<double>* out, cplx<double>* partial, int nblk, cudaStream_t st);
+cudaError_t launch_combo_dots(float4* w, const float4* const* U, int nv, const cplx<double>* coef, int64_t n,
+                              int nrhs, bool want_dots, cplx<double>* out, cplx<double>* partial, int nblk,
+                              cudaStream_t st);
   // v[c] = src[c] * s[c]
 void launch_conj(cplx<double>* v, int64_t count, cudaStream_t st);
 // w = b converted to float-float (float4 per entry), count entries.

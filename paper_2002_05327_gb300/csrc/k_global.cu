@@ -506,8 +506,9 @@ static void launch_combo_dots_nv(float4* w, const float4* const* U, const cplx<d
         combo_dots_kernel<NV, false><<<grid, DOT_NT, 0, st>>>(w, U, coef, n, nrhs, partial, nblk);
 }
 
-void launch_combo_dots(float4* w, const float4* const* U, int nv, const cplx<double>* coef, int64_t n, int nrhs,
-                       bool want_dots, cplx<double>* out, cplx<double>* partial, int nblk, cudaStream_t st) {
+cudaError_t launch_combo_dots(float4* w, const float4* const* U, int nv, const cplx<double>* coef, int64_t n,
+                              int nrhs, bool want_dots, cplx<double>* out, cplx<double>* partial, int nblk,
+                              cudaStream_t st) {
     switch (nv) {
         case 1: launch_combo_dots_nv<1>(w, U, coef, n, nrhs, want_dots, partial, nblk, st); break;
         case 2: launch_combo_dots_nv<2>(w, U, coef, n, nrhs, want_dots, partial, nblk, st); break;
@@ -517,10 +518,11 @@ void launch_combo_dots(float4* w, const float4* const* U, int nv, const cplx<dou
         case 6: launch_combo_dots_nv<6>(w, U, coef, n, nrhs, want_dots, partial, nblk, st); break;
         case 7: launch_combo_dots_nv<7>(w, U, coef, n, nrhs, want_dots, partial, nblk, st); break;
         case 8: launch_combo_dots_nv<8>(w, U, coef, n, nrhs, want_dots, partial, nblk, st); break;
-        default: return;  // the caller keeps nv in 1 .. kComboDotsMax
+        default: return cudaErrorInvalidValue;  // nv outside 1 .. kComboDotsMax: nothing launched
     }
     const int count = (want_dots ? nv : 1) * nrhs;
     dots_final_kernel<<<(count + 127) / 128, 128, 0, st>>>(partial, nblk, count, out);
+    return cudaSuccess;
 }
 
 __global__ void conj_kernel(cplx<double>* v, int64_t count) {

@@ -498,6 +498,36 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
                                           std::to_string(c->cfg.max_device_bytes) + " bytes");
     }
 
+    // ---- boxes per axis (global node ranges); edge boxes run over the global PML.
+    // Host only, before any device work, so that a bad partition is refused first.
+    std::vector<std::vector<int>> blo(3), bhi(3);
+    for (int a = 0; a < 3; ++a) {
+        if (a >= ndim) {
+            blo[a] = {0};
+            bhi[a] = {1};
+            continue;
+        }
+        std::vector<int64_t> cut(P.nb[a] + 1);
+        if (part->cuts[a]) {
+            for (int i = 0; i <= P.nb[a]; ++i) cut[i] = part->cuts[a][i];
+            if (cut[0] != 0 || cut[P.nb[a]] != c->n[a]) return fail(HELM_ERR_ARG, "cuts must span 0..n");
+        } else {
+            for (int i = 0; i <= P.nb[a]; ++i) cut[i] = (i * c->n[a]) / P.nb[a];
+        }
+        for (int i = 0; i < P.nb[a]; ++i) {
+            if (cut[i + 1] <= cut[i]) return fail(HELM_ERR_ARG, "cuts must increase");
+            blo[a].push_back(i == 0 ? 0 : (int)(Wg + cut[i]));
+            bhi[a].push_back(i == P.nb[a] - 1 ? P.N[a] : (int)(Wg + cut[i + 1]));
+            if (bhi[a].back() - blo[a].back() < P.d + 2)
+                return fail(HELM_ERR_ARG, "box narrower than overlap + 2");
+            // 3D: an inner box at least 2d wide, so that the cutoffs of at most
+            // one neighbour per axis reach a node and the assembly's list of
+            // eight boxes per node holds them all
+            if (ndim == 3 && i > 0 && i + 1 < P.nb[a] && bhi[a].back() - blo[a].back() < 2 * P.d)
+                return fail(HELM_ERR_ARG, "3D inner box narrower than twice the overlap");
+        }
+    }
+
     CK(cudaGetDevice(&c->device));
     if (c->cfg.stream) {
         c->stream = (cudaStream_t)c->cfg.stream;
@@ -546,34 +576,6 @@ int setup_impl(helm_ctx* c, int ndim, const int64_t n[3], double h, double omega
         c->dev_bytes += bytes;
         launch_stencil_ff(P, c->gwin, c->m64, c->stc_d, c->stream);
         CK(cudaGetLastError());
-    }
-    // ---- boxes per axis (global node ranges); edge boxes run over the global PML
-    std::vector<std::vector<int>> blo(3), bhi(3);
-    for (int a = 0; a < 3; ++a) {
-        if (a >= ndim) {
-            blo[a] = {0};
-            bhi[a] = {1};
-            continue;
-        }
-        std::vector<int64_t> cut(P.nb[a] + 1);
-        if (part->cuts[a]) {
-            for (int i = 0; i <= P.nb[a]; ++i) cut[i] = part->cuts[a][i];
-            if (cut[0] != 0 || cut[P.nb[a]] != c->n[a]) return fail(HELM_ERR_ARG, "cuts must span 0..n");
-        } else {
-            for (int i = 0; i <= P.nb[a]; ++i) cut[i] = (i * c->n[a]) / P.nb[a];
-        }
-        for (int i = 0; i < P.nb[a]; ++i) {
-            if (cut[i + 1] <= cut[i]) return fail(HELM_ERR_ARG, "cuts must increase");
-            blo[a].push_back(i == 0 ? 0 : (int)(Wg + cut[i]));
-            bhi[a].push_back(i == P.nb[a] - 1 ? P.N[a] : (int)(Wg + cut[i + 1]));
-            if (bhi[a].back() - blo[a].back() < P.d + 2)
-                return fail(HELM_ERR_ARG, "box narrower than overlap + 2");
-            // 3D: an inner box at least 2d wide, so that the cutoffs of at most
-            // one neighbour per axis reach a node and the assembly's list of
-            // eight boxes per node holds them all
-            if (ndim == 3 && i > 0 && i + 1 < P.nb[a] && bhi[a].back() - blo[a].back() < 2 * P.d)
-                return fail(HELM_ERR_ARG, "3D inner box narrower than twice the overlap");
-        }
     }
     std::vector<int> box_of;
     for (int a = 0; a < ndim; ++a)
